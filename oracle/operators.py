@@ -1,0 +1,109 @@
+"""Fine-level operators of the oracle as explicit scipy sparse matrices (FP64).
+
+Each matrix is assembled entry by entry from its definition; applying an
+operator is one sparse mat-vec.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import lattice
+
+
+def links(theta: np.ndarray) -> np.ndarray:
+    """U_mu(x) = exp(i theta_mu(x)) as complex [2, N], theta given as [2, L1, L0]
+    (the U(1) links of the lattice Schwinger model, Sec. I)."""
+    return np.exp(1j * theta.reshape(2, -1))
+
+
+def dirac(theta: np.ndarray, m: float) -> sp.csr_matrix:
+    """Staggered operator of Eq. staggeredD with a = 1, written out literally:
+
+        D_{x,y} = 1/2 sum_mu eta_mu(x) [U_mu(x) delta_{x+mu,y} - U_mu(x-mu)^* delta_{x-mu,y}]
+                  + m delta_{x,y},
+
+    periodic in both directions.  Duplicate (x, y) entries (extent 2) add up.
+    """
+    _, L1, L0 = theta.shape
+    N = L0 * L1
+    U = links(theta)
+    et = lattice.eta(L0, L1)
+    x0, x1 = lattice.coords(L0, L1)
+    s = np.arange(N)
+    rows, cols, vals = [s], [s], [np.full(N, m, dtype=complex)]
+    for mu in range(2):
+        d0, d1 = (1, 0) if mu == 0 else (0, 1)
+        fwd = lattice.site(x0 + d0, x1 + d1, L0, L1)
+        bwd = lattice.site(x0 - d0, x1 - d1, L0, L1)
+        rows += [s, s]
+        cols += [fwd, bwd]
+        vals += [0.5 * et[mu] * U[mu], -0.5 * et[mu] * np.conj(U[mu][bwd])]
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N)).tocsr()
+
+
+def block_split(Dm: sp.csr_matrix, L0: int, L1: int):
+    """D = B + C (Sec. II.A): B keeps the entries of D that couple two sites of
+    the same 2x2 Kaehler-Dirac block (the mass term included), C the rest."""
+    blk = lattice.kd_block(L0, L1)
+    coo = Dm.tocoo()
+    inside = blk[coo.row] == blk[coo.col]
+    N = Dm.shape[0]
+    B = sp.coo_matrix((coo.data[inside], (coo.row[inside], coo.col[inside])), shape=(N, N)).tocsr()
+    C = sp.coo_matrix((coo.data[~inside], (coo.row[~inside], coo.col[~inside])), shape=(N, N)).tocsr()
+    return B, C
+
+
+def block_inverse(B: sp.csr_matrix, L0: int, L1: int) -> sp.csr_matrix:
+    """B^-1, block by block: the 4x4 matrix of every block is gathered from B and
+    inverted with numpy.linalg.inv (LU with partial pivoting).  Requires every
+    block to be non-singular (m > 0)."""
+    blk = lattice.kd_block(L0, L1)
+    N = B.shape[0]
+    members = np.argsort(blk, kind="stable").reshape(-1, 4)   # the 4 sites of each block
+    local = np.empty(N, dtype=np.int64)
+    local[members] = np.arange(4)[None, :]
+    coo = B.tocoo()
+    dense = np.zeros((members.shape[0], 4, 4), dtype=complex)
+    np.add.at(dense, (blk[coo.row], local[coo.row], local[coo.col]), coo.data)
+    inv = np.linalg.inv(dense)
+    rows = np.repeat(members, 4, axis=1).ravel()
+    cols = np.tile(members, (1, 4)).ravel()
+    return sp.coo_matrix((inv.ravel(), (rows, cols)), shape=(N, N)).tocsr()
+
+
+class FineOperators:
+    """D, B, C, B^-1 and A = D B^-1 (Eq. defA) for one gauge field and mass, plus
+    the block-parity index sets used by the Schur system (Table kcycle)."""
+
+    def __init__(self, theta: np.ndarray, m: float):
+        _, L1, L0 = theta.shape
+        self.L0, self.L1, self.m = L0, L1, m
+        self.N = L0 * L1
+        self.D = dirac(theta, m)
+        self.B, self.C = block_split(self.D, L0, L1)
+        self.Binv = block_inverse(self.B, L0, L1)
+        self.A = (self.D @ self.Binv).tocsr()
+        self.Adag = self.A.conj().T.tocsr()
+        par = lattice.kd_parity(L0, L1)
+        self.even = np.nonzero(par == 0)[0]
+        self.odd = np.nonzero(par == 1)[0]
+        self.A_eo = self.A[self.even][:, self.odd].tocsr()
+        self.A_oe = self.A[self.odd][:, self.even].tocsr()
+        self.eps = lattice.epsilon(L0, L1)
+
+    def schur(self, xe: np.ndarray) -> np.ndarray:
+        """S x_e = x_e - A_eo A_oe x_e (Table kcycle, level-1 operator)."""
+        return xe - self.A_eo @ (self.A_oe @ xe)
+
+    def schur_rhs(self, b: np.ndarray) -> np.ndarray:
+        """b_e - A_eo b_o: right-hand side of the Schur system for A z = b."""
+        return b[self.even] - self.A_eo @ b[self.odd]
+
+    def reconstruct(self, b: np.ndarray, ze: np.ndarray) -> np.ndarray:
+        """Full solution of D x = b from z_e: z_o = b_o - A_oe z_e, x = B^-1 z."""
+        z = np.zeros(self.N, dtype=complex)
+        z[self.even] = ze
+        z[self.odd] = b[self.odd] - self.A_oe @ ze
+        return self.Binv @ z

@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
+
+This module generates inputs only: U(1) gauge fields from a heatbath of the
+Wilson plaquette action and complex Gaussian vectors.  It holds none of the
+multigrid method's arithmetic (no Dirac operator, no transfer, no solver).
+
+Random numbers come from one counter-based generator, SplitMix64
+(Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+OOPSLA 2014): the n-th 64-bit output of stream ``seed`` is
+``mix(seed + (n + 1) * 0x9E3779B97F4A7C15)`` with the SplitMix64 finaliser
+``mix``.  Gaussians use the Box-Muller transform of two such uniforms.
+Everything is plain vectorised numpy, so the same seed gives the same field on
+any machine.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser on a uint64 array (wraps modulo 2**64)."""
+    z = np.asarray(z, dtype=np.uint64)
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Outputs number ``counters`` (uint64 array) of the SplitMix64 stream ``seed``."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        state = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (c + np.uint64(1)) * GOLDEN
+    return _mix(state)
+
+
+def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Doubles in (0, 1]: the top 53 bits of the SplitMix64 output, plus one ulp."""
+    u = splitmix64(seed, counters)
+    return ((u >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+
+
+def stream_seed(seed: int, *keys: int) -> int:
+    """Derives an independent stream seed from ``seed`` and integer keys."""
+    s = np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
+    for k in keys:
+        with np.errstate(over="ignore"):
+            s = _mix(s ^ np.uint64(k & 0xFFFFFFFFFFFFFFFF)) + GOLDEN
+    return int(s[0])
+
+
+def gaussian_complex(seed: int, n: int) -> np.ndarray:
+    """n complex numbers with independent N(0,1) real and imaginary parts.
+
+    Element j takes uniforms 2j and 2j+1 of stream ``seed``;
+    Box-Muller: re = r cos(2 pi u2), im = r sin(2 pi u2), r = sqrt(-2 ln u1).
+    """
+    j = np.arange(n, dtype=np.uint64)
+    u1 = uniform01(seed, 2 * j)
+    u2 = uniform01(seed, 2 * j + np.uint64(1))
+    r = np.sqrt(-2.0 * np.log(u1))
+    t = 2.0 * np.pi * u2
+    return r * np.cos(t) + 1j * r * np.sin(t)
+
+
+def gaussian_source(seed: int, L0: int, L1: int) -> np.ndarray:
+    """A complex Gaussian fermion source as a [L1, L0] complex128 array."""
+    return gaussian_complex(seed, L0 * L1).reshape(L1, L0)
+
+
+def _von_mises(seed: int, ctr0: int, kappa: np.ndarray, max_attempts: int = 64) -> np.ndarray:
+    """Samples angles with density proportional to exp(kappa cos t), t in (-pi, pi].
+
+    Best and Fisher (1979), "Efficient simulation of the von Mises distribution",
+    Appl. Statist. 28, 152: rejection from a wrapped Cauchy envelope.  Element i,
+    attempt a uses uniforms ctr0 + (a * n + i) * 3 + {0, 1, 2}.  A sample that is
+    still rejected after ``max_attempts`` is drawn uniformly (probability far below
+    1e-30 at the couplings used here).
+    """
+    n = kappa.size
+    out = np.empty(n)
+    small = kappa < 1e-8
+    kap = np.where(small, 1.0, kappa)
+    tau = 1.0 + np.sqrt(1.0 + 4.0 * kap * kap)
+    rho = (tau - np.sqrt(2.0 * tau)) / (2.0 * kap)
+    r = (1.0 + rho * rho) / (2.0 * rho)
+    todo = np.arange(n)
+    for a in range(max_attempts):
+        if todo.size == 0:
+            break
+        base = np.uint64(ctr0) + (np.uint64(a) * np.uint64(n) + todo.astype(np.uint64)) * np.uint64(3)
+        u1 = uniform01(seed, base)
+        u2 = uniform01(seed, base + np.uint64(1))
+        u3 = uniform01(seed, base + np.uint64(2))
+        rr = r[todo]
+        z = np.cos(np.pi * u1)
+        f = (1.0 + rr * z) / (rr + z)
+        c = kap[todo] * (rr - f)
+        ok = (c * (2.0 - c) - u2 > 0.0) | (np.log(c / u2) + 1.0 - c >= 0.0)
+        ok |= small[todo]
+        ang = np.where(u3 > 0.5, 1.0, -1.0) * np.arccos(np.clip(f, -1.0, 1.0))
+        ang = np.where(small[todo], np.pi * (2.0 * u3 - 1.0), ang)
+        acc = todo[ok]
+        out[acc] = ang[ok]
+        todo = todo[~ok]
+    if todo.size:
+        base = np.uint64(ctr0) + np.uint64(max_attempts * n * 3) + todo.astype(np.uint64)
+        out[todo] = np.pi * (2.0 * uniform01(seed, base) - 1.0)
+    return out
+
+
+def heatbath_u1(L0: int, L1: int, beta: float, sweeps: int, seed: int) -> np.ndarray:
+    """Quenched compact U(1) gauge field theta[mu, x1, x0] after ``sweeps`` heatbath sweeps.
+
+    Action S = beta * sum_plaquettes (1 - cos theta_p) with
+    theta_p(x) = theta_0(x) + theta_1(x + 0hat) - theta_0(x + 1hat) - theta_1(x).
+    Each link is redrawn from its exact conditional (von Mises) distribution
+    given its two staples.  A sweep visits theta_0 on rows x1 even, then x1 odd,
+    then theta_1 on columns x0 even, then x0 odd: links inside one such set share
+    no plaquette, so they update together.  Cold start (theta = 0).  Periodic.
+    """
+    if L0 % 2 or L1 % 2:
+        raise ValueError("heatbath needs even extents")
+    th = np.zeros((2, L1, L0))
+    nl = (L0 * L1) // 2
+    for sw in range(sweeps):
+        for ps in range(4):
+            mu, par = ps // 2, ps % 2
+            t0, t1 = th[0], th[1]
+            if mu == 0:
+                # plaquette at x:      theta_0(x) + [t1(x+0) - t0(x+1) - t1(x)]
+                # plaquette at x-1hat: [t0(x-1) + t1(x-1+0) - t1(x-1)] - theta_0(x)
+                a = np.roll(t1, -1, axis=1) - np.roll(t0, -1, axis=0) - t1
+                t0m = np.roll(t0, 1, axis=0)
+                t1m = np.roll(t1, 1, axis=0)
+                b = t0m + np.roll(t1m, -1, axis=1) - t1m
+                rows = slice(par, None, 2)
+                a, b = a[rows, :], b[rows, :]
+            else:
+                # plaquette at x:      theta_1(x+0)... for link theta_1(x):
+                #   theta_p(x)      = t0(x) + t1(x+0) - t0(x+1) - theta_1(x)  -> -(theta - a')
+                #   theta_p(x-0hat) = t0(x-0) + theta_1(x) - t0(x-0+1) - t1(x-0) -> theta + b'
+                a = t0 + np.roll(t1, -1, axis=1) - np.roll(t0, -1, axis=0)
+                t0m = np.roll(t0, 1, axis=1)
+                b = t0m - np.roll(t0m, -1, axis=0) - np.roll(t1, 1, axis=1)
+                cols = (slice(None), slice(par, None, 2))
+                a, b = a[cols], b[cols]
+            # weight exp(beta * [cos(theta + a) + cos(theta - b)]) for mu = 0;
+            # for mu = 1: exp(beta * [cos(theta - a) + cos(theta + b)]).
+            if mu == 0:
+                k = np.exp(1j * a) + np.exp(-1j * b)
+            else:
+                k = np.exp(-1j * a) + np.exp(1j * b)
+            kap = beta * np.abs(k).ravel()
+            psi = np.angle(k).ravel()
+            ctr0 = (sw * 4 + ps) * (nl * 3 * 65)
+            t = _von_mises(seed, ctr0, kap)
+            newv = np.angle(np.exp(1j * (t - psi))).reshape(a.shape)
+            if mu == 0:
+                th[0][rows, :] = newv
+            else:
+                th[1][cols] = newv
+    return th
+
+
+def plaquette_mean(theta: np.ndarray) -> float:
+    """Average cos(theta_p) over all plaquettes (input-quality diagnostic)."""
+    t0, t1 = theta[0], theta[1]
+    tp = t0 + np.roll(t1, -1, axis=1) - np.roll(t0, -1, axis=0) - t1
+    return float(np.mean(np.cos(tp)))
+
+
+def gauge_transform(theta: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    """Links of the gauge-rotated field U^g_mu(x) = g(x) U_mu(x) g(x+mu)^*, g = exp(i alpha)."""
+    t = theta.copy()
+    t[0] = theta[0] + alpha - np.roll(alpha, -1, axis=1)
+    t[1] = theta[1] + alpha - np.roll(alpha, -1, axis=0)
+    return t
