@@ -1,0 +1,296 @@
+"""Python binding of libsw (include/sw.h): ctypes argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays may be
+numpy arrays (host memory, on_device = 0) or torch CUDA tensors (device
+memory, on_device = 1); complex fields are complex128 (complex64 for the FP32
+Dslash).  All compute runs in the CUDA library; there is no fallback: if
+libsw.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "SwError", "lib", "SW_OP_D", "SW_OP_DDAG", "SW_OP_A", "SW_OP_ADAG", "SW_OP_S",
+    "SW_PREC_FP64", "SW_PREC_FP32", "sw_context_create", "sw_context_free", "sw_last_error",
+    "sw_gauge_load", "sw_gauge_free", "sw_dslash", "sw_mg_params_default", "sw_mg_setup",
+    "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
+    "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_coarse", "sw_mg_transfer",
+    "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
+]
+
+SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S = 0, 1, 2, 3, 4
+SW_PREC_FP64, SW_PREC_FP32 = 0, 1
+ERRORS = {0: "SW_OK", -1: "SW_ERR_ARG", -2: "SW_ERR_SHAPE", -3: "SW_ERR_OOM", -4: "SW_ERR_NOCONV",
+          -5: "SW_ERR_BREAKDOWN", -6: "SW_ERR_NAN", -7: "SW_ERR_CUDA", -8: "SW_ERR_TIMEOUT"}
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsw.so")
+
+
+class SwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sw_mg_params(ctypes.Structure):
+    _fields_ = [("setup_maxiter", ctypes.c_int), ("setup_tol", ctypes.c_double),
+                ("setup_passes", ctypes.c_int), ("outer_restart", ctypes.c_int),
+                ("outer_maxiter", ctypes.c_int), ("smoother_iters", ctypes.c_int),
+                ("omega", ctypes.c_double), ("inter_restart", ctypes.c_int),
+                ("inter_maxiter", ctypes.c_int), ("inter_tol", ctypes.c_double),
+                ("coarsest_maxiter", ctypes.c_int), ("coarsest_tol", ctypes.c_double)]
+
+
+class sw_solve_stats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("fine_applies", ctypes.c_longlong),
+                ("inter_iters", ctypes.c_longlong), ("inter_solves", ctypes.c_longlong),
+                ("coarsest_iters", ctypes.c_longlong), ("coarsest_solves", ctypes.c_longlong),
+                ("true_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+
+
+def lib():
+    """The loaded libsw.so (raises if it is not built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "sw_context_create": (_I, [_I, _VP, ctypes.POINTER(_VP)]),
+            "sw_context_free": (None, [_VP]),
+            "sw_last_error": (ctypes.c_char_p, [_VP]),
+            "sw_gauge_load": (_I, [_VP, _I, _I, _VP, _I, ctypes.POINTER(_VP)]),
+            "sw_gauge_free": (None, [_VP]),
+            "sw_dslash": (_I, [_VP, _D, _I, _I, _VP, _VP, _I]),
+            "sw_mg_params_default": (None, [ctypes.POINTER(sw_mg_params)]),
+            "sw_mg_setup": (_I, [_VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(sw_mg_params), ctypes.c_uint64,
+                                 ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+            "sw_mg_free": (None, [_VP]),
+            "sw_mg_solve": (_I, [_VP, _VP, _VP, _D, _I, ctypes.POINTER(sw_solve_stats)]),
+            "sw_mg_solve_batch": (_I, [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(sw_solve_stats)]),
+            "sw_debug_maps": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
+            "sw_mg_level_info": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                      ctypes.POINTER(_I)]),
+            "sw_mg_export_P": (_I, [_VP, _I, _VP]),
+            "sw_mg_export_Y": (_I, [_VP, _I, _VP]),
+            "sw_mg_apply_coarse": (_I, [_VP, _I, _I, _VP, _VP, _I]),
+            "sw_mg_transfer": (_I, [_VP, _I, _I, _VP, _VP, _I]),
+            "sw_stream_seed": (ctypes.c_uint64, [ctypes.c_uint64, _I, _I]),
+            "sw_set_timing": (_I, [_VP, _I]),
+            "sw_kernel_times": (_I, [_VP, _I, _VP, _VP]),
+            "sw_launch_count": (ctypes.c_longlong, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class _Handle:
+    """An object returned by the library, with the context it reports errors to."""
+
+    def __init__(self, ptr, ctx_ptr, free):
+        self.ptr, self.ctx_ptr, self._free = ptr, ctx_ptr, free
+
+    def free(self):
+        if self.ptr:
+            self._free(self.ptr)
+            self.ptr = None
+
+
+def _check(rc, ctx_ptr, allow=()):
+    if rc != 0 and rc not in allow:
+        msg = lib().sw_last_error(ctx_ptr)
+        raise SwError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _same_place(*arrs):
+    places = {_ptr(a)[1] for a in arrs}
+    if len(places) != 1:
+        raise ValueError("all buffers of one call must be on the host or all on the device")
+    return places.pop()
+
+
+def sw_context_create(device: int = 0, stream=None) -> _Handle:
+    """stream: a raw cudaStream_t value (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    out = _VP()
+    rc = lib().sw_context_create(device, stream or None, ctypes.byref(out))
+    if rc != 0:
+        raise SwError(rc, "sw_context_create failed")
+    return _Handle(out, out, lib().sw_context_free)
+
+
+def sw_context_free(ctx: _Handle):
+    ctx.free()
+
+
+def sw_last_error(ctx: _Handle) -> str:
+    return lib().sw_last_error(ctx.ptr).decode()
+
+
+def sw_gauge_load(ctx: _Handle, theta) -> _Handle:
+    """theta: float64 [2, L1, L0] link angles (numpy or torch CUDA tensor)."""
+    L1, L0 = int(theta.shape[1]), int(theta.shape[2])
+    p, dev = _ptr(theta)
+    out = _VP()
+    _check(lib().sw_gauge_load(ctx.ptr, L0, L1, p, dev, ctypes.byref(out)), ctx.ptr)
+    h = _Handle(out, ctx.ptr, lib().sw_gauge_free)
+    h.shape = (L1, L0)
+    return h
+
+
+def sw_gauge_free(g: _Handle):
+    g.free()
+
+
+def sw_dslash(g: _Handle, mass: float, op: int, precision: int, inp, out):
+    dev = _same_place(inp, out)
+    _check(lib().sw_dslash(g.ptr, float(mass), op, precision, _ptr(inp)[0], _ptr(out)[0], dev),
+           g.ctx_ptr)
+    return out
+
+
+def sw_mg_params_default() -> sw_mg_params:
+    p = sw_mg_params()
+    lib().sw_mg_params_default(ctypes.byref(p))
+    return p
+
+
+def sw_mg_setup(g: _Handle, mass: float, levels: int, block, nvec, params=None, seed: int = 0,
+                psi0=None) -> _Handle:
+    """block: [(b0, b1)] * (levels-1); nvec: [nv] * (levels-1); psi0: None or a list
+    of numpy complex128 arrays [nvec[l], ndof_l] (vector-major)."""
+    blk = (_I * (2 * (levels - 1)))(*[int(v) for b in block for v in b])
+    nv = (_I * (levels - 1))(*[int(v) for v in nvec])
+    keep = []
+    ps = None
+    if psi0 is not None:
+        ps = (_VP * (levels - 1))()
+        for l, arr in enumerate(psi0):
+            a = np.ascontiguousarray(arr, dtype=np.complex128)
+            keep.append(a)
+            ps[l] = a.ctypes.data
+    out = _VP()
+    prm = ctypes.byref(params) if params is not None else None
+    _check(lib().sw_mg_setup(g.ptr, float(mass), levels, blk, nv, prm, seed, ps,
+                             ctypes.byref(out)), g.ctx_ptr)
+    return _Handle(out, g.ctx_ptr, lib().sw_mg_free)
+
+
+def sw_mg_free(mg: _Handle):
+    mg.free()
+
+
+def sw_mg_solve(mg: _Handle, b, x, tol: float, allow_noconv: bool = False) -> dict:
+    dev = _same_place(b, x)
+    st = sw_solve_stats()
+    rc = _check(lib().sw_mg_solve(mg.ptr, _ptr(b)[0], _ptr(x)[0], float(tol), dev,
+                                  ctypes.byref(st)), mg.ctx_ptr,
+                allow=(-4,) if allow_noconv else ())
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def sw_mg_solve_batch(mg: _Handle, B, X, tol: float, allow_noconv: bool = False):
+    dev = _same_place(B, X)
+    nrhs = int(B.shape[0])
+    st = (sw_solve_stats * max(nrhs, 1))()
+    _check(lib().sw_mg_solve_batch(mg.ptr, nrhs, _ptr(B)[0], _ptr(X)[0], float(tol), dev, st),
+           mg.ctx_ptr, allow=(-4,) if allow_noconv else ())
+    return [st[k].as_dict() for k in range(nrhs)]
+
+
+def sw_debug_maps(g: _Handle, a0: int, a1: int) -> dict:
+    L1, L0 = g.shape
+    N = L0 * L1
+    out = {k: np.zeros(n, dtype=np.int32) for k, n in
+           (("eta", 2 * N), ("eps", N), ("kd_block", N), ("kd_parity", N), ("agg", N))}
+    _check(lib().sw_debug_maps(g.ptr, a0, a1, *[out[k].ctypes.data for k in
+                                                ("eta", "eps", "kd_block", "kd_parity", "agg")]),
+           g.ctx_ptr)
+    out["eta"] = out["eta"].reshape(2, N)
+    return out
+
+
+def sw_mg_level_info(mg: _Handle, level: int):
+    e0, e1, nc = _I(), _I(), _I()
+    _check(lib().sw_mg_level_info(mg.ptr, level, ctypes.byref(e0), ctypes.byref(e1),
+                                  ctypes.byref(nc)), mg.ctx_ptr)
+    return e0.value, e1.value, nc.value
+
+
+def sw_mg_export_P(mg: _Handle, level: int, nv: int) -> np.ndarray:
+    e0, e1, nc = sw_mg_level_info(mg, level)
+    P = np.zeros((e0 * e1 * nc, nv), dtype=np.complex128)
+    _check(lib().sw_mg_export_P(mg.ptr, level, P.ctypes.data), mg.ctx_ptr)
+    return P
+
+
+def sw_mg_export_Y(mg: _Handle, level: int) -> np.ndarray:
+    e0, e1, nc = sw_mg_level_info(mg, level)
+    Y = np.zeros((e0 * e1, 5, nc, nc), dtype=np.complex128)
+    _check(lib().sw_mg_export_Y(mg.ptr, level, Y.ctypes.data), mg.ctx_ptr)
+    return Y
+
+
+def sw_mg_apply_coarse(mg: _Handle, level: int, dagger: int, inp, out):
+    dev = _same_place(inp, out)
+    _check(lib().sw_mg_apply_coarse(mg.ptr, level, dagger, _ptr(inp)[0], _ptr(out)[0], dev),
+           mg.ctx_ptr)
+    return out
+
+
+def sw_mg_transfer(mg: _Handle, level: int, direction: int, inp, out):
+    dev = _same_place(inp, out)
+    _check(lib().sw_mg_transfer(mg.ptr, level, direction, _ptr(inp)[0], _ptr(out)[0], dev),
+           mg.ctx_ptr)
+    return out
+
+
+def sw_stream_seed(seed: int, level: int, index: int) -> int:
+    return int(lib().sw_stream_seed(seed, level, index))
+
+
+def sw_set_timing(ctx: _Handle, enable: bool):
+    _check(lib().sw_set_timing(ctx.ptr, 1 if enable else 0), ctx.ptr)
+
+
+def sw_kernel_times(ctx: _Handle, n: int = 4):
+    """[(launches, total ms)] per timing category (0: fine S, l: coarse level l+1)."""
+    cnt = np.zeros(n, dtype=np.int64)
+    ms = np.zeros(n, dtype=np.float64)
+    _check(lib().sw_kernel_times(ctx.ptr, n, cnt.ctypes.data, ms.ctypes.data), ctx.ptr)
+    return [(int(a), float(b)) for a, b in zip(cnt, ms)]
+
+
+def sw_launch_count() -> int:
+    return int(lib().sw_launch_count())

@@ -1,0 +1,313 @@
+// Fine-level kernels: staggered Dslash (Eq. staggeredD), Kaehler-Dirac block
+// inverse B^-1 (Sec. II.A, Eq. localblock), the block hopping term C, and the
+// compositions A = D B^-1 = I + C B^-1 (Eq. defA), A^dag and the Schur
+// operator I - A_eo A_oe (Table kcycle).
+//
+// Links are stored pre-multiplied as W_mu(s) = eta_mu(s) U_mu(s) / 2.  In 2D
+// eta_mu(s - mu) = eta_mu(s) (eta_1 depends on x0 only), so the backward hop of
+// Eq. staggeredD is -conj(W_mu(s - mu)) x(s - mu).
+#include "sw_internal.h"
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {  // acc += a b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfmac(double2& acc, double2 a, double2 b) {  // acc += conj(a) b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// Lexicographic Dslash: out(s) = m in(s) + sg * sum_mu [W_mu(s) in(s+mu) - conj(W_mu(s-mu)) in(s-mu)]
+// sg = +1 for D, -1 for D^dag (D - m is anti-Hermitian, Sec. II).
+// One thread per site; consecutive threads take consecutive x0, so every
+// load of in and W is coalesced; neighbour values are re-read from L1/L2.
+template <typename C2, typename R>
+__global__ void __launch_bounds__(256) k_dslash_lex(const C2* __restrict__ in, C2* __restrict__ out,
+                                                    const C2* __restrict__ W, R mass, R sg, int L0,
+                                                    int L1) {
+  int x0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int x1 = blockIdx.y;
+  if (x0 >= L0) return;
+  long N = (long)L0 * L1;
+  long row = (long)x1 * L0;
+  long s = row + x0;
+  long sp0 = row + (x0 + 1 == L0 ? 0 : x0 + 1);
+  long sm0 = row + (x0 == 0 ? L0 - 1 : x0 - 1);
+  long sp1 = (long)(x1 + 1 == L1 ? 0 : x1 + 1) * L0 + x0;
+  long sm1 = (long)(x1 == 0 ? L1 - 1 : x1 - 1) * L0 + x0;
+  C2 xs = __ldg(in + s);
+  C2 a = __ldg(in + sp0), b = __ldg(in + sm0), c = __ldg(in + sp1), d = __ldg(in + sm1);
+  C2 w0 = __ldg(W + s), w1 = __ldg(W + N + s);
+  C2 w0m = __ldg(W + sm0), w1m = __ldg(W + N + sm1);
+  R hx = 0, hy = 0;
+  // forward hops: + W x
+  hx = fma(w0.x, a.x, hx); hx = fma(-w0.y, a.y, hx);
+  hy = fma(w0.x, a.y, hy); hy = fma(w0.y, a.x, hy);
+  hx = fma(w1.x, c.x, hx); hx = fma(-w1.y, c.y, hx);
+  hy = fma(w1.x, c.y, hy); hy = fma(w1.y, c.x, hy);
+  // backward hops: - conj(W) x
+  hx = fma(-w0m.x, b.x, hx); hx = fma(-w0m.y, b.y, hx);
+  hy = fma(-w0m.x, b.y, hy); hy = fma(w0m.y, b.x, hy);
+  hx = fma(-w1m.x, d.x, hx); hx = fma(-w1m.y, d.y, hx);
+  hy = fma(-w1m.x, d.y, hy); hy = fma(w1m.y, d.x, hy);
+  C2 o;
+  o.x = fma(sg, hx, mass * xs.x);
+  o.y = fma(sg, hy, mass * xs.y);
+  out[s] = o;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_pack(const double2* __restrict__ lex, double2* __restrict__ ps, int L0, int L1) {
+  int N = L0 * L1;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int x0 = s % L0, x1 = s / L0;
+  ps[ps_index(x0, x1, L0, N)] = lex[s];
+}
+__global__ void k_unpack(const double2* __restrict__ ps, double2* __restrict__ lex, int L0, int L1) {
+  int N = L0 * L1;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int x0 = s % L0, x1 = s / L0;
+  lex[s] = ps[ps_index(x0, x1, L0, N)];
+}
+
+// ---------------------------------------------------------------------------
+// B^-1 per KD block.  B is D restricted to the 2x2 block with corner at even
+// coordinates, mass included (Sec. II.A).  Site k of the block sits at
+// (2X0 + (k & 1), 2X1 + (k >> 1)).  For direction mu the partner inside the
+// block of site k is k ^ (1 << mu): a forward hop (coefficient W_mu(s)) when
+// x_mu is even, a backward hop (coefficient -conj(W_mu(s - mu))) when odd.
+// Inverted by Gauss-Jordan elimination with partial pivoting in FP64.
+__global__ void k_binv_build(const double2* __restrict__ Wps, double mass, double2* __restrict__ binv,
+                             int L0, int L1) {
+  int N = L0 * L1;
+  int nb = N >> 2;
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double2 M[4][4], I[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      M[i][j] = make_double2(i == j ? mass : 0.0, 0.0);
+      I[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+  int x0b, x1b;
+  ps_coords(4 * b, L0, N, x0b, x1b);  // site k = 0 of the block
+  for (int k = 0; k < 4; ++k) {
+    int x0 = x0b + (k & 1), x1 = x1b + (k >> 1);
+    for (int mu = 0; mu < 2; ++mu) {
+      int kp = k ^ (1 << mu);
+      int xm = mu == 0 ? x0 : x1;
+      if ((xm & 1) == 0) {
+        M[k][kp] = Wps[mu * N + 4 * b + k];
+      } else {
+        double2 w = Wps[mu * N + 4 * b + kp];  // W_mu(s - mu), s - mu is site kp
+        M[k][kp] = make_double2(-w.x, w.y);
+      }
+    }
+  }
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    double best = hypot(M[c][c].x, M[c][c].y);
+    for (int r = c + 1; r < 4; ++r) {
+      double v = hypot(M[r][c].x, M[r][c].y);
+      if (v > best) { best = v; p = r; }
+    }
+    if (p != c)
+      for (int j = 0; j < 4; ++j) {
+        double2 t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t;
+        t = I[c][j]; I[c][j] = I[p][j]; I[p][j] = t;
+      }
+    double2 piv = M[c][c];
+    double den = piv.x * piv.x + piv.y * piv.y;
+    double2 inv = make_double2(piv.x / den, -piv.y / den);
+    for (int j = 0; j < 4; ++j) { M[c][j] = cmul(M[c][j], inv); I[c][j] = cmul(I[c][j], inv); }
+    for (int r = 0; r < 4; ++r) {
+      if (r == c) continue;
+      double2 f = M[r][c];
+      for (int j = 0; j < 4; ++j) {
+        double2 a = cmul(f, M[c][j]), e = cmul(f, I[c][j]);
+        M[r][j].x -= a.x; M[r][j].y -= a.y;
+        I[r][j].x -= e.x; I[r][j].y -= e.y;
+      }
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) binv[16 * b + 4 * i + j] = I[i][j];
+}
+
+// out = M in (or M^dag in) on every KD block of one parity half.
+__global__ void k_block_apply(const double2* __restrict__ M, const double2* __restrict__ in,
+                              double2* __restrict__ out, int nblk, int dagger) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  double2 v[4];
+  for (int j = 0; j < 4; ++j) v[j] = in[4 * b + j];
+  const double2* m = M + 16 * b;
+  for (int i = 0; i < 4; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (!dagger)
+      for (int j = 0; j < 4; ++j) cfma(acc, m[4 * i + j], v[j]);
+    else
+      for (int j = 0; j < 4; ++j) cfmac(acc, m[4 * j + i], v[j]);
+    out[4 * b + i] = acc;
+  }
+}
+
+// (C in)(s) for a site s of parity half par: the two hops of s that leave its
+// KD block.  in is the opposite parity half.
+__device__ __forceinline__ double2 hop_out(const double2* __restrict__ Wps,
+                                           const double2* __restrict__ in, int f, int L0, int L1,
+                                           int N) {
+  int x0, x1;
+  ps_coords(f, L0, N, x0, x1);
+  int half = N >> 1;
+  double2 acc = make_double2(0.0, 0.0);
+  // direction 0
+  if (x0 & 1) {  // forward neighbour is in the next block
+    int t = ps_index(x0 + 1 == L0 ? 0 : x0 + 1, x1, L0, N);
+    cfma(acc, Wps[f], in[t % half]);
+  } else {
+    int t = ps_index(x0 == 0 ? L0 - 1 : x0 - 1, x1, L0, N);
+    double2 w = Wps[t];
+    double2 v = in[t % half];
+    acc.x -= w.x * v.x + w.y * v.y;
+    acc.y -= w.x * v.y - w.y * v.x;
+  }
+  // direction 1
+  if (x1 & 1) {
+    int t = ps_index(x0, x1 + 1 == L1 ? 0 : x1 + 1, L0, N);
+    cfma(acc, Wps[N + f], in[t % half]);
+  } else {
+    int t = ps_index(x0, x1 == 0 ? L1 - 1 : x1 - 1, L0, N);
+    double2 w = Wps[N + t];
+    double2 v = in[t % half];
+    acc.x -= w.x * v.x + w.y * v.y;
+    acc.y -= w.x * v.y - w.y * v.x;
+  }
+  return acc;
+}
+
+__global__ void k_hop(const double2* __restrict__ Wps, int par, double sign,
+                      const double2* __restrict__ src, const double2* __restrict__ in,
+                      double2* __restrict__ out, int L0, int L1) {
+  int N = L0 * L1, half = N >> 1;
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= half) return;
+  double2 c = hop_out(Wps, in, par * half + h, L0, L1, N);
+  double2 o = src ? src[h] : make_double2(0.0, 0.0);
+  o.x = fma(sign, c.x, o.x);
+  o.y = fma(sign, c.y, o.y);
+  out[h] = o;
+}
+
+__global__ void k_hop_block(const double2* __restrict__ Wps, const double2* __restrict__ M,
+                            int par, int dagger, double sign, const double2* __restrict__ src,
+                            const double2* __restrict__ in, double2* __restrict__ out, int L0,
+                            int L1) {
+  int N = L0 * L1, half = N >> 1;
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= (half >> 2)) return;
+  double2 u[4];
+  for (int k = 0; k < 4; ++k) u[k] = hop_out(Wps, in, par * half + 4 * b + k, L0, L1, N);
+  const double2* m = M + 16 * b;
+  for (int i = 0; i < 4; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (!dagger)
+      for (int j = 0; j < 4; ++j) cfma(acc, m[4 * i + j], u[j]);
+    else
+      for (int j = 0; j < 4; ++j) cfmac(acc, m[4 * j + i], u[j]);
+    double2 o = src ? src[4 * b + i] : make_double2(0.0, 0.0);
+    o.x = fma(sign, acc.x, o.x);
+    o.y = fma(sign, acc.y, o.y);
+    out[4 * b + i] = o;
+  }
+}
+
+inline int nblocks(long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_dslash_lex(const sw_gauge* g, double mass, int dagger, const double2* in, double2* out,
+                       cudaStream_t s) {
+  dim3 grid(nblocks(g->L0, 256), g->L1);
+  k_dslash_lex<double2, double><<<grid, 256, 0, s>>>(in, out, g->W_lex, mass, dagger ? -1.0 : 1.0,
+                                                     g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_dslash_lex32(const sw_gauge* g, float mass, int dagger, const float2* in, float2* out,
+                         cudaStream_t s) {
+  dim3 grid(nblocks(g->L0, 256), g->L1);
+  k_dslash_lex<float2, float><<<grid, 256, 0, s>>>(in, out, g->W_lex32, mass, dagger ? -1.0f : 1.0f,
+                                                   g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_pack(const sw_gauge* g, const double2* lex, double2* ps, cudaStream_t s) {
+  k_pack<<<nblocks(g->N, 256), 256, 0, s>>>(lex, ps, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_unpack(const sw_gauge* g, const double2* ps, double2* lex, cudaStream_t s) {
+  k_unpack<<<nblocks(g->N, 256), 256, 0, s>>>(ps, lex, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_binv_build(const sw_gauge* g, double mass, double2* binv, cudaStream_t s) {
+  k_binv_build<<<nblocks(g->N / 4, 128), 128, 0, s>>>(g->W_ps, mass, binv, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_block_apply(const sw_gauge* g, const double2* binv, int par, int dagger,
+                        const double2* in, double2* out, cudaStream_t s) {
+  int nblk = g->N / 8;
+  k_block_apply<<<nblocks(nblk, 128), 128, 0, s>>>(binv + (long)par * nblk * 16, in, out, nblk,
+                                                   dagger);
+  SW_LAUNCH_CHECK();
+}
+void launch_hop(const sw_gauge* g, int par, double sign, const double2* src, const double2* in,
+                double2* out, cudaStream_t s) {
+  k_hop<<<nblocks(g->N / 2, 256), 256, 0, s>>>(g->W_ps, par, sign, src, in, out, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_hop_block(const sw_gauge* g, const double2* binv, int par, int dagger, double sign,
+                      const double2* src, const double2* in, double2* out, cudaStream_t s) {
+  int nblk = g->N / 8;
+  k_hop_block<<<nblocks(nblk, 128), 128, 0, s>>>(g->W_ps, binv + (long)par * nblk * 16, par, dagger,
+                                                 sign, src, in, out, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+
+// A x = x + C B^-1 x on a full parity-split vector: t = B^-1 x per block, then
+// y_p = x_p + C_{p,1-p} t_{1-p} for p = even, odd.
+void fine_apply_A(const sw_gauge* g, const double2* binv, const double2* in, double2* out,
+                  double2* tmp, cudaStream_t s) {
+  long half = g->N / 2;
+  launch_block_apply(g, binv, 0, 0, in, tmp, s);
+  launch_block_apply(g, binv, 1, 0, in + half, tmp + half, s);
+  launch_hop(g, 0, 1.0, in, tmp + half, out, s);
+  launch_hop(g, 1, 1.0, in + half, tmp, out + half, s);
+}
+// A^dag x = x + B^-dag C^dag x = x - B^-dag C x (C is anti-Hermitian).
+void fine_apply_Adag(const sw_gauge* g, const double2* binv, const double2* in, double2* out,
+                     cudaStream_t s) {
+  long half = g->N / 2;
+  launch_hop_block(g, binv, 0, 1, -1.0, in, in + half, out, s);
+  launch_hop_block(g, binv, 1, 1, -1.0, in + half, in, out + half, s);
+}
+// S x_e = x_e - A_eo A_oe x_e with A_oe = C_oe B_e^-1 and A_eo = C_eo B_o^-1
+// (A_ee = A_oo = I on KD-block parity):
+//   t_e = B_e^-1 x_e;  v_o = B_o^-1 C_oe t_e;  y_e = x_e - C_eo v_o.
+void fine_apply_S(const sw_gauge* g, const double2* binv, const double2* in_e, double2* out_e,
+                  double2* tmp, cudaStream_t s) {
+  long half = g->N / 2;
+  launch_block_apply(g, binv, 0, 0, in_e, tmp, s);
+  launch_hop_block(g, binv, 1, 0, 1.0, nullptr, tmp, tmp + half, s);
+  launch_hop(g, 0, -1.0, in_e, tmp + half, out_e, s);
+}

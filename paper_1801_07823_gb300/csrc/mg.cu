@@ -1,0 +1,476 @@
+// Multigrid hierarchy: setup and K-cycle solve (Sec. IV, Table kcycle).
+//
+// Setup per level l (0 = fine): nv near-null vectors psi = psi0 + e, e from CG
+// on A A^dag e = -A A^dag psi0 (tolerance setup_tol, setup_maxiter
+// iterations); global modified Gram-Schmidt; chiral doubling and modified
+// Gram-Schmidt per (aggregate, chirality) -> P; Galerkin stencil
+// Y = P^dag A P and its adjoint stencil.
+//
+// Solve: flexible GCR(outer_restart) on S z_e = b_e - A_eo b_o with
+// S = I - A_eo A_oe, preconditioned by the K-cycle: MR(smoother_iters, omega)
+// on S; restrict (r_e, 0); GCR(inter_restart, max inter_maxiter, tol
+// inter_tol) on A_hat preconditioned by the next K-cycle, or CGNE (tol
+// coarsest_tol, max coarsest_maxiter) on the coarsest level; prolong and keep
+// the even part; r2 = r1 - S e; MR post-smoother on r2; p = x1 + e + x3.
+// Then z_o = b_o - A_oe z_e and x = B^-1 z.
+//
+// Krylov coefficients stay on the device (Coef slots); the host reads back
+// only the residual norms its stopping tests branch on.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "sw_internal.h"
+#include "sw_mg.h"
+
+namespace {
+
+double2* dalloc(long n) {
+  void* p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(double2));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw SwError{SW_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(n * 16) +
+                                  " bytes failed: " + cudaGetErrorString(e)};
+  }
+  return (double2*)p;
+}
+
+}  // namespace
+
+void sw_mg_release(sw_mg* mg) {
+  for (double2* p : mg->allocs) cudaFree(p);
+  mg->allocs.clear();
+}
+
+double2* mg_alloc(sw_mg* mg, long n) {
+  double2* p = dalloc(n);
+  mg->allocs.push_back(p);
+  return p;
+}
+
+// ---------------------------------------------------------------- operators
+long level_len(const sw_mg* mg, int l) {
+  const MgLevel& L = mg->lev[l];
+  return l == 0 ? mg->g->N / 2 : L.ndof;
+}
+
+// Operator of level l in the solve: S on level 0 (even half), A_hat below.
+// skip: optional device flag that turns the (coarse) application into a no-op.
+void level_op(sw_mg* mg, int l, const double2* in, double2* out, const int* skip = nullptr) {
+  sw_ctx* c = mg->ctx;
+  int tk = timing_begin(c, l);
+  if (l == 0) {
+    fine_apply_S(mg->g, mg->binv, in, out, mg->lev[0].stmp, c->stream);
+    mg->st_fine_applies++;
+  } else {
+    const MgLevel& L = mg->lev[l];
+    launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, in, out, c->stream, skip,
+                        c->timing ? c->exec + l : nullptr);
+  }
+  timing_end(c, tk);
+}
+void level_opdag(sw_mg* mg, int l, const double2* in, double2* out, const int* skip = nullptr) {
+  sw_ctx* c = mg->ctx;
+  const MgLevel& L = mg->lev[l];
+  int tk = timing_begin(c, l);
+  launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Yd, in, out, c->stream, skip,
+                      c->timing ? c->exec + l : nullptr);
+  timing_end(c, tk);
+}
+// Normal operator used by the setup on level l: A A^dag (full fine vectors on
+// level 0).
+void level_normal(sw_mg* mg, int l, const double2* in, double2* out, double2* tmp) {
+  cudaStream_t s = mg->ctx->stream;
+  if (l == 0) {
+    fine_apply_Adag(mg->g, mg->binv, in, tmp, s);
+    fine_apply_A(mg->g, mg->binv, tmp, out, mg->lev[0].stmp, s);
+  } else {
+    level_opdag(mg, l, in, tmp);
+    level_op(mg, l, tmp, out);
+  }
+}
+
+static void check_norm(double v, const char* where) {
+  if (!std::isfinite(v)) throw SwError{SW_ERR_NAN, std::string("non-finite norm in ") + where};
+}
+
+// ---------------------------------------------------------------- Krylov
+// MR smoother with zero initial guess: x, r = b - op x.
+static void mr(sw_mg* mg, int l, const double2* b, double2* x, double2* r, double2* q) {
+  sw_ctx* c = mg->ctx;
+  long n = level_len(mg, l);
+  int sq = slot_base(l) + 8, sqq = slot_base(l) + 9;
+  blas_zero(c, x, n);
+  blas_copy(c, r, b, n);
+  double om = mg->p.omega;
+  for (int it = 0; it < mg->p.smoother_iters; ++it) {
+    level_op(mg, l, r, q);
+    blas_dot(c, q, r, n, sq);
+    blas_norm2(c, q, n, sqq);
+    blas_axpy(c, x, r, n, coef_ratio(sq, sqq, om));
+    blas_axpy(c, r, q, n, coef_ratio(sq, sqq, -om));
+  }
+}
+
+static void solve_level(sw_mg* mg, int l, const double2* rhs, double2* sol);
+
+// K-cycle preconditioner of level l: out = M(r).
+static void kcycle(sw_mg* mg, int l, const double2* r, double2* out) {
+  sw_ctx* c = mg->ctx;
+  MgLevel& L = mg->lev[l];
+  MgLevel& C = mg->lev[l + 1];
+  long n = level_len(mg, l);
+  cudaStream_t s = c->stream;
+  mr(mg, l, r, L.kx1, L.kr1, L.kq);
+  if (l == 0)
+    launch_restrict_fine(mg->g, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s);
+  else
+    launch_restrict_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s);
+  solve_level(mg, l + 1, C.rhs, C.sol);
+  if (l == 0)
+    launch_prolong_fine(mg->g, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s);
+  else
+    launch_prolong_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s);
+  level_op(mg, l, L.ke, L.kq);
+  blas_sub(c, L.kr2, L.kr1, L.kq, n);
+  mr(mg, l, L.kr2, L.kx3, L.kr3, L.kq);
+  blas_add3(c, out, L.kx1, L.ke, L.kx3, n);
+}
+
+struct GcrResult {
+  int iters, restarts;
+  bool converged;
+};
+
+// Flexible restarted GCR on level l (see the oracle's fgcr for the steps).
+static GcrResult fgcr(sw_mg* mg, int l, const double2* b, double2* x, double tol_abs, int restart,
+                      int maxiter, bool confirm) {
+  sw_ctx* c = mg->ctx;
+  MgLevel& L = mg->lev[l];
+  long n = level_len(mg, l);
+  int sb = slot_base(l);
+  int s_rr = sb + 0, s_qq = sb + 2, s_a = sb + 3, s_b = sb + 4;
+  blas_zero(c, x, n);
+  blas_copy(c, L.gr, b, n);
+  int k = 0, it = 0, restarts = 0;
+  for (;;) {
+    blas_norm2(c, L.gr, n, s_rr);
+    double rn = std::sqrt(slot_read(c, s_rr).x);
+    check_norm(rn, "GCR residual");
+    if (rn <= tol_abs) {
+      if (!confirm) return GcrResult{it, restarts, true};
+      level_op(mg, l, x, L.gtmp);
+      blas_sub(c, L.gtmp, b, L.gtmp, n);
+      blas_norm2(c, L.gtmp, n, s_rr);
+      double rt = std::sqrt(slot_read(c, s_rr).x);
+      check_norm(rt, "GCR true residual");
+      if (rt <= tol_abs) return GcrResult{it, restarts, true};
+      blas_copy(c, L.gr, L.gtmp, n);
+      k = 0;
+      ++restarts;
+      continue;
+    }
+    if (it >= maxiter) return GcrResult{it, restarts, false};
+    double2* p = L.gp[k];
+    double2* q = L.gq[k];
+    if (l + 1 < mg->nlev)
+      kcycle(mg, l, L.gr, p);
+    else
+      blas_copy(c, p, L.gr, n);
+    level_op(mg, l, p, q);
+    for (int j = 0; j < k; ++j) {
+      blas_dot(c, L.gq[j], q, n, s_b);
+      blas_axpy(c, q, L.gq[j], n, coef_ratio(s_b, -1, -1.0));
+      blas_axpy(c, p, L.gp[j], n, coef_ratio(s_b, -1, -1.0));
+    }
+    blas_norm2(c, q, n, s_qq);
+    blas_scale(c, q, n, coef_ratio(-1, s_qq, 1.0, COEF_SQRT_DEN));
+    blas_scale(c, p, n, coef_ratio(-1, s_qq, 1.0, COEF_SQRT_DEN));
+    blas_dot(c, q, L.gr, n, s_a);
+    blas_axpy(c, x, p, n, coef_ratio(s_a, -1, 1.0));
+    blas_axpy(c, L.gr, q, n, coef_ratio(s_a, -1, -1.0));
+    ++k;
+    ++it;
+    if (l == 1 && mg->verbose > 1) std::fprintf(stderr, "[sw]   level-2 GCR %d |r| %.3e (tol %.3e)\n", it, rn, tol_abs);
+    if (l == 0 && mg->verbose)
+      std::fprintf(stderr, "[sw] outer %d |r| %.3e  inter %lld/%lld coarsest %lld/%lld\n", it, rn,
+                   mg->st_inter_iters, mg->st_inter_solves, mg->st_coarsest_iters,
+                   mg->st_coarsest_solves);
+    if (k == restart && it < maxiter) {
+      level_op(mg, l, x, L.gtmp);
+      blas_sub(c, L.gr, b, L.gtmp, n);
+      k = 0;
+      ++restarts;
+    }
+  }
+}
+
+// CG on the normal error (Craig): x = op^dag y with op op^dag y = b.  The
+// stopping test runs on the device (iter_check); the host queues kIterBatch
+// iterations at a time and reads the control block between batches, so the
+// iterations need no host round trip.  Iterates and counts are those of the
+// sequential loop: every kernel after the stopping iteration is a no-op.
+constexpr int kIterBatch = 8;
+
+static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
+  sw_ctx* c = mg->ctx;
+  MgLevel& L = mg->lev[l];
+  long n = level_len(mg, l);
+  int sb = slot_base(l);
+  int s_rr[2] = {sb + 10, sb + 11}, s_pp = sb + 12;
+  int* ctl = c->ctl + 4 * l;
+  int maxit = mg->p.coarsest_maxiter;
+  blas_zero(c, x, n);
+  blas_copy(c, L.gr, b, n);
+  blas_norm2(c, L.gr, n, s_rr[0]);
+  double rr = slot_read(c, s_rr[0]).x;
+  check_norm(rr, "CGNE residual");
+  double stop = mg->p.coarsest_tol * std::sqrt(rr);
+  level_opdag(mg, l, L.gr, L.cp);
+  iter_init(c, ctl, s_rr[0], stop, maxit);
+  int cur = 0;
+  for (int issued = 0;;) {
+    for (int q = 0; q < kIterBatch && issued < maxit; ++q, ++issued) {
+      blas_norm2(c, L.cp, n, s_pp, ctl);
+      blas_axpy(c, x, L.cp, n, coef_ratio(s_rr[cur], s_pp, 1.0), ctl);
+      level_op(mg, l, L.cp, L.cw, ctl);
+      blas_axpy(c, L.gr, L.cw, n, coef_ratio(s_rr[cur], s_pp, -1.0), ctl);
+      blas_norm2(c, L.gr, n, s_rr[1 - cur], ctl);
+      iter_check(c, ctl, s_rr[1 - cur], stop, maxit);
+      level_opdag(mg, l, L.gr, L.cw, ctl);
+      blas_xpay(c, L.cp, L.cw, n, coef_ratio(s_rr[1 - cur], s_rr[cur], 1.0), ctl);
+      cur = 1 - cur;
+    }
+    iter_read(c, ctl, c->h_ctl);
+    if (c->h_ctl[2]) throw SwError{SW_ERR_NAN, "non-finite norm in CGNE residual"};
+    if (c->h_ctl[0] || issued >= maxit) break;
+  }
+  return c->h_ctl[1];
+}
+
+static void solve_level(sw_mg* mg, int l, const double2* rhs, double2* sol) {
+  sw_ctx* c = mg->ctx;
+  if (l == mg->nlev - 1) {
+    mg->st_coarsest_iters += cgne(mg, l, rhs, sol);
+    mg->st_coarsest_solves++;
+    return;
+  }
+  long n = level_len(mg, l);
+  int s = slot_base(l) + 1;
+  blas_norm2(c, rhs, n, s);
+  double bn = std::sqrt(slot_read(c, s).x);
+  check_norm(bn, "intermediate right-hand side");
+  GcrResult r = fgcr(mg, l, rhs, sol, mg->p.inter_tol * bn, mg->p.inter_restart,
+                     mg->p.inter_maxiter, false);
+  mg->st_inter_iters += r.iters;
+  mg->st_inter_solves++;
+}
+
+// CG on a Hermitian positive semi-definite normal operator (setup).
+static int cg_setup(sw_mg* mg, int l, const double2* b, double2* x) {
+  sw_ctx* c = mg->ctx;
+  MgLevel& L = mg->lev[l];
+  long n = L.ndof;
+  int sb = slot_base(l);
+  int s_rr[2] = {sb + 20, sb + 21}, s_pq = sb + 22;
+  blas_zero(c, x, n);
+  blas_copy(c, L.sr, b, n);
+  blas_copy(c, L.sp, L.sr, n);
+  blas_norm2(c, L.sr, n, s_rr[0]);
+  double rr = slot_read(c, s_rr[0]).x;
+  check_norm(rr, "setup CG residual");
+  double stop = mg->p.setup_tol * std::sqrt(rr);
+  int k = 0, cur = 0;
+  while (k < mg->p.setup_maxiter && std::sqrt(rr) > stop) {
+    level_normal(mg, l, L.sp, L.sq, L.st);
+    blas_dot(c, L.sp, L.sq, n, s_pq);
+    blas_axpy(c, x, L.sp, n, coef_ratio(s_rr[cur], s_pq, 1.0));
+    blas_axpy(c, L.sr, L.sq, n, coef_ratio(s_rr[cur], s_pq, -1.0));
+    blas_norm2(c, L.sr, n, s_rr[1 - cur]);
+    rr = slot_read(c, s_rr[1 - cur]).x;
+    check_norm(rr, "setup CG residual");
+    blas_xpay(c, L.sp, L.sr, n, coef_ratio(s_rr[1 - cur], s_rr[cur], 1.0));
+    cur = 1 - cur;
+    ++k;
+  }
+  return k;
+}
+
+// ---------------------------------------------------------------- setup
+void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
+  sw_ctx* c = mg->ctx;
+  sw_gauge* g = mg->g;
+  cudaStream_t s = c->stream;
+  long N = g->N;
+  mg->binv = mg_alloc(mg, N * 4);
+  launch_binv_build(g, mg->mass, mg->binv, s);
+  mg->lev[0].stmp = mg_alloc(mg, N);
+  for (int l = 0; l + 1 < mg->nlev; ++l) {
+    MgLevel& L = mg->lev[l];
+    MgLevel& C = mg->lev[l + 1];
+    int nv = L.nv;
+    long n = L.ndof;
+    // work vectors of the setup
+    L.sr = mg_alloc(mg, n); L.sp = mg_alloc(mg, n); L.sq = mg_alloc(mg, n);
+    L.st = mg_alloc(mg, n);
+    double2* V = mg_alloc(mg, n * nv);
+    double2* e = mg_alloc(mg, n);
+    double2* start = mg_alloc(mg, n);
+    double2* lex = l == 0 ? mg_alloc(mg, n) : nullptr;
+    int sb = slot_base(l);
+    for (int i = 0; i < nv; ++i) {
+      double2* target = l == 0 ? lex : start;
+      if (psi0 && psi0[l]) {
+        SW_CUDA(cudaMemcpyAsync(target, psi0[l] + 2 * (long)i * n, n * sizeof(double2),
+                                cudaMemcpyHostToDevice, s));
+      } else {
+        launch_gaussian(sw_stream_seed(seed, l, i), n, target, s);
+      }
+      if (l == 0) launch_pack(g, lex, start, s);
+      double2* psi = V + (long)i * n;
+      for (int pass = 0; pass < mg->p.setup_passes; ++pass) {
+        if (pass > 0) {
+          blas_copy(c, start, psi, n);
+          blas_norm2(c, start, n, sb + 30);
+          blas_scale(c, start, n, coef_ratio(-1, sb + 30, 1.0, COEF_SQRT_DEN));
+        }
+        level_normal(mg, l, start, L.sq, L.st);
+        blas_zero(c, L.sp, n);
+        blas_sub(c, L.st, L.sp, L.sq, n);  // r = -A A^dag start
+        int its = cg_setup(mg, l, L.st, e);  // L.st is read before CG reuses it
+        mg->setup_iters.push_back(its);
+        blas_copy(c, psi, start, n);  // psi = psi0 + e
+        blas_axpy(c, psi, e, n, coef_const(1.0));
+      }
+    }
+    // global modified Gram-Schmidt in index order
+    for (int i = 0; i < nv; ++i) {
+      double2* vi = V + (long)i * n;
+      for (int j = 0; j < i; ++j) {
+        blas_dot(c, V + (long)j * n, vi, n, sb + 31);
+        blas_axpy(c, vi, V + (long)j * n, n, coef_ratio(sb + 31, -1, -1.0));
+      }
+      blas_norm2(c, vi, n, sb + 32);
+      double nn = slot_read(c, sb + 32).x;
+      if (!(nn > 0.0) || !std::isfinite(nn))
+        throw SwError{SW_ERR_BREAKDOWN, "global Gram-Schmidt: vector " + std::to_string(i) +
+                                            " on level " + std::to_string(l + 1) + " has norm 0"};
+      blas_scale(c, vi, n, coef_ratio(-1, sb + 32, 1.0, COEF_SQRT_DEN));
+    }
+    // chiral doubling + block orthonormalisation
+    L.P = mg_alloc(mg, n * nv);
+    SW_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), s));
+    if (l == 0)
+      launch_block_ortho_fine(g, L.b0, L.b1, nv, V, L.P, c->flag, s);
+    else
+      launch_block_ortho_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, nv, V, L.P, c->flag, s);
+    int hflag = 0;
+    SW_CUDA(cudaMemcpyAsync(&hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SW_CUDA(cudaStreamSynchronize(s));
+    if (hflag)
+      throw SwError{SW_ERR_BREAKDOWN,
+                    "block orthonormalisation met a zero vector on level " + std::to_string(l + 1)};
+    // Galerkin coarse operator and its adjoint stencil
+    long ysz = (long)C.E0 * C.E1 * 5 * C.nc * C.nc;
+    C.Y = mg_alloc(mg, ysz);
+    C.Yd = mg_alloc(mg, ysz);
+    if (l == 0) {
+      double2* Wv = mg_alloc(mg, N * 2 * nv);
+      launch_build_W(g, nv, mg->binv, L.P, Wv, s);
+      launch_build_Y_fine(g, mg->mass, L.b0, L.b1, nv, L.P, Wv, C.Y, s);
+    } else {
+      double2* T = mg_alloc(mg, (long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
+      launch_build_Y_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, nv, L.Y, L.P, T, C.Y, s);
+    }
+    launch_build_Ydag(CoarseGeom{C.E0, C.E1, C.nc}, C.Y, C.Yd, s);
+    SW_CUDA(cudaStreamSynchronize(s));
+  }
+  // solve workspace
+  for (int l = 0; l < mg->nlev; ++l) {
+    MgLevel& L = mg->lev[l];
+    long n = level_len(mg, l);
+    L.rhs = mg_alloc(mg, n);
+    L.sol = mg_alloc(mg, n);
+    L.gr = mg_alloc(mg, n);
+    L.gtmp = mg_alloc(mg, n);
+    int nb = l == 0 ? mg->p.outer_restart : mg->p.inter_restart;
+    if (l == mg->nlev - 1) nb = 0;
+    L.gp.assign(nb, nullptr);
+    L.gq.assign(nb, nullptr);
+    for (int k = 0; k < nb; ++k) { L.gp[k] = mg_alloc(mg, n); L.gq[k] = mg_alloc(mg, n); }
+    L.cp = mg_alloc(mg, n);
+    L.cw = mg_alloc(mg, n);
+    if (l + 1 < mg->nlev) {
+      L.kx1 = mg_alloc(mg, n); L.kr1 = mg_alloc(mg, n); L.kq = mg_alloc(mg, n);
+      L.ke = mg_alloc(mg, n); L.kr2 = mg_alloc(mg, n); L.kx3 = mg_alloc(mg, n);
+      L.kr3 = mg_alloc(mg, n);
+    }
+    if (l == 0) {
+      mg->bps = mg_alloc(mg, N);
+      mg->xps = mg_alloc(mg, N);
+      mg->lexb = mg_alloc(mg, N);
+      mg->lexx = mg_alloc(mg, N);
+      mg->lext = mg_alloc(mg, N);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- solve
+int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
+                    sw_solve_stats* st) {
+  sw_ctx* c = mg->ctx;
+  sw_gauge* g = mg->g;
+  cudaStream_t s = c->stream;
+  long N = g->N, half = N / 2;
+  auto t0 = std::chrono::steady_clock::now();
+  mg->st_fine_applies = mg->st_inter_iters = mg->st_inter_solves = 0;
+  mg->st_coarsest_iters = mg->st_coarsest_solves = 0;
+  MgLevel& L = mg->lev[0];
+  launch_pack(g, b_lex, mg->bps, s);
+  int sb = slot_base(0);
+  blas_norm2(c, mg->bps, N, sb + 40);
+  double bn = std::sqrt(slot_read(c, sb + 40).x);
+  check_norm(bn, "right-hand side");
+  if (bn == 0.0) {
+    blas_zero(c, x_lex, N);
+    SW_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+      std::memset(st, 0, sizeof(*st));
+      st->converged = 1;
+    }
+    return SW_OK;
+  }
+  // b~_e = b_e - A_eo b_o = b_e - C_eo B_o^-1 b_o
+  launch_block_apply(g, mg->binv, 1, 0, mg->bps + half, L.stmp + half, s);
+  launch_hop(g, 0, -1.0, mg->bps, L.stmp + half, L.rhs, s);
+  GcrResult r = fgcr(mg, 0, L.rhs, L.sol, tol * bn, mg->p.outer_restart, mg->p.outer_maxiter, true);
+  // z_o = b_o - C_oe B_e^-1 z_e ; x = B^-1 z
+  launch_block_apply(g, mg->binv, 0, 0, L.sol, L.stmp, s);
+  launch_hop(g, 1, -1.0, mg->bps + half, L.stmp, L.stmp + half, s);
+  launch_block_apply(g, mg->binv, 0, 0, L.sol, mg->xps, s);
+  launch_block_apply(g, mg->binv, 1, 0, L.stmp + half, mg->xps + half, s);
+  launch_unpack(g, mg->xps, x_lex, s);
+  // true residual ||b - D x|| / ||b|| in FP64
+  launch_dslash_lex(g, mg->mass, 0, x_lex, mg->lext, s);
+  blas_sub(c, mg->lext, b_lex, mg->lext, N);
+  blas_norm2(c, mg->lext, N, sb + 41);
+  double tr = std::sqrt(slot_read(c, sb + 41).x) / bn;
+  auto t1 = std::chrono::steady_clock::now();
+  if (st) {
+    st->converged = r.converged ? 1 : 0;
+    st->outer_iters = r.iters;
+    st->restarts = r.restarts;
+    st->fine_applies = mg->st_fine_applies;
+    st->inter_iters = mg->st_inter_iters;
+    st->inter_solves = mg->st_inter_solves;
+    st->coarsest_iters = mg->st_coarsest_iters;
+    st->coarsest_solves = mg->st_coarsest_solves;
+    st->true_resid = tr;
+    st->seconds = std::chrono::duration<double>(t1 - t0).count();
+  }
+  return r.converged ? SW_OK : SW_ERR_NOCONV;
+}

@@ -1,0 +1,52 @@
+// Multigrid hierarchy object shared by mg.cu and api.cu.
+#pragma once
+#include <vector>
+
+#include "sw_internal.h"
+
+// One level of the hierarchy.  Level 0 is the fine lattice (dof = site,
+// parity-split order); level l > 0 is a coarse lattice E0 x E1 with nc dof per
+// site (dof = X * nc + k).  b0, b1, nv and P describe the transfer from this
+// level to level l + 1.
+struct MgLevel {
+  int E0 = 0, E1 = 0, nc = 1;
+  long ndof = 0;
+  int b0 = 0, b1 = 0, nv = 0;
+  double2* P = nullptr;   // [ndof][nv]
+  double2* Y = nullptr;   // stencil of this level (l > 0), see coarse.cu
+  double2* Yd = nullptr;  // stencil of the adjoint
+  // setup work vectors
+  double2 *sr = nullptr, *sp = nullptr, *sq = nullptr, *st = nullptr;
+  // solve work vectors
+  double2 *rhs = nullptr, *sol = nullptr, *gr = nullptr, *gtmp = nullptr;
+  double2 *cp = nullptr, *cw = nullptr;
+  std::vector<double2*> gp, gq;
+  double2 *kx1 = nullptr, *kr1 = nullptr, *kq = nullptr, *ke = nullptr, *kr2 = nullptr;
+  double2 *kx3 = nullptr, *kr3 = nullptr;
+  double2* stmp = nullptr;  // [N] scratch of the fine operators (level 0)
+};
+
+struct sw_mg {
+  sw_ctx* ctx = nullptr;
+  sw_gauge* g = nullptr;
+  double mass = 0.0;
+  sw_mg_params p{};
+  int nlev = 0;
+  int verbose = 0;  // SW_VERBOSE=1: a stderr line per outer iteration; 2: also level 2
+  double2* binv = nullptr;
+  std::vector<MgLevel> lev;
+  std::vector<double2*> allocs;
+  double2 *bps = nullptr, *xps = nullptr, *lexb = nullptr, *lexx = nullptr, *lext = nullptr;
+  std::vector<int> setup_iters;
+  long long st_fine_applies = 0, st_inter_iters = 0, st_inter_solves = 0;
+  long long st_coarsest_iters = 0, st_coarsest_solves = 0;
+};
+
+// Device scalar slots owned by level l: [64 l, 64 l + 64).
+inline int slot_base(int l) { return 64 * l; }
+
+double2* mg_alloc(sw_mg* mg, long n);
+void sw_mg_release(sw_mg* mg);
+void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed);
+int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
+                    sw_solve_stats* st);

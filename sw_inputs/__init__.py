@@ -9,8 +9,9 @@ Random numbers come from one counter-based generator, SplitMix64
 OOPSLA 2014): the n-th 64-bit output of stream ``seed`` is
 ``mix(seed + (n + 1) * 0x9E3779B97F4A7C15)`` with the SplitMix64 finaliser
 ``mix``.  Gaussians use the Box-Muller transform of two such uniforms.
-Everything is plain vectorised numpy, so the same seed gives the same field on
-any machine.
+Vectors are plain numpy; the gauge heatbath runs with torch float64 on the CPU
+or a CUDA device (same algorithm and counters; the field is a deterministic
+function of the seed and the device type).
 """
 from __future__ import annotations
 
@@ -71,48 +72,90 @@ def gaussian_source(seed: int, L0: int, L1: int) -> np.ndarray:
     return gaussian_complex(seed, L0 * L1).reshape(L1, L0)
 
 
-def _von_mises(seed: int, ctr0: int, kappa: np.ndarray, max_attempts: int = 64) -> np.ndarray:
+_MASK = {k: (1 << (64 - k)) - 1 for k in (11, 27, 30, 31)}
+
+
+def _tmix(z):
+    """SplitMix64 finaliser on an int64 torch tensor (two's-complement wrap,
+    logical right shifts by masking)."""
+    z = (z ^ ((z >> 30) & _MASK[30])) * _as_i64(0xBF58476D1CE4E5B9)
+    z = (z ^ ((z >> 27) & _MASK[27])) * _as_i64(0x94D049BB133111EB)
+    return z ^ ((z >> 31) & _MASK[31])
+
+
+def _as_i64(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def torch_uniform01(seed: int, counters):
+    """Same values as ``uniform01`` for int64 torch counters (any device)."""
+    state = _as_i64(seed) + (counters + 1) * _as_i64(0x9E3779B97F4A7C15)
+    u = _tmix(state)
+    return (((u >> 11) & _MASK[11]).double() + 1.0) * (2.0 ** -53)
+
+
+def _von_mises(seed: int, ctr0: int, kappa, max_attempts: int = 64):
     """Samples angles with density proportional to exp(kappa cos t), t in (-pi, pi].
 
     Best and Fisher (1979), "Efficient simulation of the von Mises distribution",
     Appl. Statist. 28, 152: rejection from a wrapped Cauchy envelope.  Element i,
     attempt a uses uniforms ctr0 + (a * n + i) * 3 + {0, 1, 2}.  A sample that is
     still rejected after ``max_attempts`` is drawn uniformly (probability far below
-    1e-30 at the couplings used here).
+    1e-30 at the couplings used here).  kappa: float64 torch tensor.
     """
-    n = kappa.size
-    out = np.empty(n)
+    import torch
+    n = kappa.numel()
+    dev = kappa.device
+    out = torch.zeros(n, dtype=torch.float64, device=dev)
     small = kappa < 1e-8
-    kap = np.where(small, 1.0, kappa)
-    tau = 1.0 + np.sqrt(1.0 + 4.0 * kap * kap)
-    rho = (tau - np.sqrt(2.0 * tau)) / (2.0 * kap)
+    kap = torch.where(small, torch.ones_like(kappa), kappa)
+    tau = 1.0 + torch.sqrt(1.0 + 4.0 * kap * kap)
+    rho = (tau - torch.sqrt(2.0 * tau)) / (2.0 * kap)
     r = (1.0 + rho * rho) / (2.0 * rho)
-    todo = np.arange(n)
-    for a in range(max_attempts):
-        if todo.size == 0:
-            break
-        base = np.uint64(ctr0) + (np.uint64(a) * np.uint64(n) + todo.astype(np.uint64)) * np.uint64(3)
-        u1 = uniform01(seed, base)
-        u2 = uniform01(seed, base + np.uint64(1))
-        u3 = uniform01(seed, base + np.uint64(2))
-        rr = r[todo]
-        z = np.cos(np.pi * u1)
+    idx = torch.arange(n, device=dev)
+
+    def attempt(a, sel):
+        base = ctr0 + (a * n + sel) * 3
+        u1 = torch_uniform01(seed, base)
+        u2 = torch_uniform01(seed, base + 1)
+        u3 = torch_uniform01(seed, base + 2)
+        rr = r[sel]
+        z = torch.cos(torch.pi * u1)
         f = (1.0 + rr * z) / (rr + z)
-        c = kap[todo] * (rr - f)
-        ok = (c * (2.0 - c) - u2 > 0.0) | (np.log(c / u2) + 1.0 - c >= 0.0)
-        ok |= small[todo]
-        ang = np.where(u3 > 0.5, 1.0, -1.0) * np.arccos(np.clip(f, -1.0, 1.0))
-        ang = np.where(small[todo], np.pi * (2.0 * u3 - 1.0), ang)
-        acc = todo[ok]
-        out[acc] = ang[ok]
+        c = kap[sel] * (rr - f)
+        ok = (c * (2.0 - c) - u2 > 0.0) | (torch.log(c / u2) + 1.0 - c >= 0.0)
+        sm = small[sel]
+        ok = ok | sm
+        ang = torch.where(u3 > 0.5, 1.0, -1.0) * torch.arccos(torch.clamp(f, -1.0, 1.0))
+        ang = torch.where(sm, torch.pi * (2.0 * u3 - 1.0), ang)
+        return ok, ang
+
+    # The first attempts run on every element without compaction (no host
+    # synchronisation); an element keeps the angle of its first accepted attempt,
+    # which is what the one-at-a-time rejection loop gives.
+    accepted = torch.zeros(n, dtype=torch.bool, device=dev)
+    first = min(8, max_attempts)
+    for a in range(first):
+        ok, ang = attempt(a, idx)
+        take = ok & ~accepted
+        out = torch.where(take, ang, out)
+        accepted |= ok
+    todo = idx[~accepted]
+    for a in range(first, max_attempts):
+        if todo.numel() == 0:
+            break
+        ok, ang = attempt(a, todo)
+        out[todo[ok]] = ang[ok]
         todo = todo[~ok]
-    if todo.size:
-        base = np.uint64(ctr0) + np.uint64(max_attempts * n * 3) + todo.astype(np.uint64)
-        out[todo] = np.pi * (2.0 * uniform01(seed, base) - 1.0)
+    if todo.numel():
+        base = ctr0 + max_attempts * n * 3 + todo
+        out[todo] = torch.pi * (2.0 * torch_uniform01(seed, base) - 1.0)
     return out
 
 
-def heatbath_u1(L0: int, L1: int, beta: float, sweeps: int, seed: int) -> np.ndarray:
+def heatbath_u1(L0: int, L1: int, beta: float, sweeps: int, seed: int,
+                device: str = "cpu") -> np.ndarray:
     """Quenched compact U(1) gauge field theta[mu, x1, x0] after ``sweeps`` heatbath sweeps.
 
     Action S = beta * sum_plaquettes (1 - cos theta_p) with
@@ -121,49 +164,46 @@ def heatbath_u1(L0: int, L1: int, beta: float, sweeps: int, seed: int) -> np.nda
     given its two staples.  A sweep visits theta_0 on rows x1 even, then x1 odd,
     then theta_1 on columns x0 even, then x0 odd: links inside one such set share
     no plaquette, so they update together.  Cold start (theta = 0).  Periodic.
+    Runs with torch float64 on ``device`` ("cpu" or "cuda"); the field is a
+    deterministic function of (seed, device type).
     """
+    import torch
     if L0 % 2 or L1 % 2:
         raise ValueError("heatbath needs even extents")
-    th = np.zeros((2, L1, L0))
+    th = torch.zeros((2, L1, L0), dtype=torch.float64, device=device)
     nl = (L0 * L1) // 2
     for sw in range(sweeps):
         for ps in range(4):
             mu, par = ps // 2, ps % 2
             t0, t1 = th[0], th[1]
             if mu == 0:
-                # plaquette at x:      theta_0(x) + [t1(x+0) - t0(x+1) - t1(x)]
-                # plaquette at x-1hat: [t0(x-1) + t1(x-1+0) - t1(x-1)] - theta_0(x)
-                a = np.roll(t1, -1, axis=1) - np.roll(t0, -1, axis=0) - t1
-                t0m = np.roll(t0, 1, axis=0)
-                t1m = np.roll(t1, 1, axis=0)
-                b = t0m + np.roll(t1m, -1, axis=1) - t1m
-                rows = slice(par, None, 2)
-                a, b = a[rows, :], b[rows, :]
+                # plaquette at x:      theta + [t1(x+0) - t0(x+1) - t1(x)]          = theta + a
+                # plaquette at x-1hat: [t0(x-1) + t1(x-1+0) - t1(x-1)] - theta     = b - theta
+                a = torch.roll(t1, -1, 1) - torch.roll(t0, -1, 0) - t1
+                t0m = torch.roll(t0, 1, 0)
+                t1m = torch.roll(t1, 1, 0)
+                b = t0m + torch.roll(t1m, -1, 1) - t1m
+                a, b = a[par::2, :], b[par::2, :]
+                k = torch.exp(1j * a) + torch.exp(-1j * b)
             else:
-                # plaquette at x:      theta_1(x+0)... for link theta_1(x):
-                #   theta_p(x)      = t0(x) + t1(x+0) - t0(x+1) - theta_1(x)  -> -(theta - a')
-                #   theta_p(x-0hat) = t0(x-0) + theta_1(x) - t0(x-0+1) - t1(x-0) -> theta + b'
-                a = t0 + np.roll(t1, -1, axis=1) - np.roll(t0, -1, axis=0)
-                t0m = np.roll(t0, 1, axis=1)
-                b = t0m - np.roll(t0m, -1, axis=0) - np.roll(t1, 1, axis=1)
-                cols = (slice(None), slice(par, None, 2))
-                a, b = a[cols], b[cols]
-            # weight exp(beta * [cos(theta + a) + cos(theta - b)]) for mu = 0;
-            # for mu = 1: exp(beta * [cos(theta - a) + cos(theta + b)]).
-            if mu == 0:
-                k = np.exp(1j * a) + np.exp(-1j * b)
-            else:
-                k = np.exp(-1j * a) + np.exp(1j * b)
-            kap = beta * np.abs(k).ravel()
-            psi = np.angle(k).ravel()
+                # plaquette at x:      [t0(x) + t1(x+0) - t0(x+1)] - theta          = a - theta
+                # plaquette at x-0hat: theta + [t0(x-0) - t0(x-0+1) - t1(x-0)]     = theta + b
+                a = t0 + torch.roll(t1, -1, 1) - torch.roll(t0, -1, 0)
+                t0m = torch.roll(t0, 1, 1)
+                b = t0m - torch.roll(t0m, -1, 0) - torch.roll(t1, 1, 1)
+                a, b = a[:, par::2], b[:, par::2]
+                k = torch.exp(-1j * a) + torch.exp(1j * b)
+            # weight exp(beta |k| cos(theta + arg k)): theta = t - arg k, t ~ von Mises(beta |k|)
+            kap = (beta * torch.abs(k)).reshape(-1)
+            psi = torch.angle(k).reshape(-1)
             ctr0 = (sw * 4 + ps) * (nl * 3 * 65)
             t = _von_mises(seed, ctr0, kap)
-            newv = np.angle(np.exp(1j * (t - psi))).reshape(a.shape)
+            newv = torch.angle(torch.exp(1j * (t - psi))).reshape(a.shape)
             if mu == 0:
-                th[0][rows, :] = newv
+                th[0][par::2, :] = newv
             else:
-                th[1][cols] = newv
-    return th
+                th[1][:, par::2] = newv
+    return th.cpu().numpy()
 
 
 def plaquette_mean(theta: np.ndarray) -> float:

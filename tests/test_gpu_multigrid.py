@@ -1,0 +1,237 @@
+"""GPU parity of the multigrid setup, transfers, coarse stencil and solve."""
+import numpy as np
+import pytest
+
+import sw_inputs as si
+from oracle import lattice, operators
+from oracle import mg as omg
+from tests.gpu_helpers import assemble_stencil, compact_P, psi0_arrays, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import paper_1801_07823_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sw):
+    c = sw.sw_context_create(0)
+    yield c
+    c.free()
+
+
+def params(sw, **kw):
+    p = sw.sw_mg_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# (L, levels, blocks, nvec): coarse extents 1, 2, 3 and a 3-level case
+CASES = [
+    (8, 2, [(4, 4)], [4]),
+    (16, 2, [(4, 4)], [6]),
+    (24, 2, [(4, 4)], [5]),
+    (32, 3, [(4, 4), (2, 2)], [6, 8]),
+    (24, 3, [(2, 2), (3, 3)], [4, 5]),
+]
+
+
+@pytest.mark.parametrize("L,levels,blocks,nvec", CASES)
+def test_setup_parity_fixed_cg(sw, ctx, L, levels, blocks, nvec):
+    """P and A_hat = P^dag A P agree with the oracle when both run the same fixed
+    number of CG steps per null vector (no stopping-test ambiguity)."""
+    m = 0.08
+    th = si.heatbath_u1(L, L, 3.0, 10, seed=L + levels, device="cuda")
+    psi0 = psi0_arrays(L, L, nvec, levels, blocks)
+    pr = params(sw, setup_tol=0.0, setup_maxiter=8)
+    H = omg.Hierarchy(th, m, levels, blocks, nvec,
+                      [list(a) for a in psi0], omg.Params(setup_tol=0.0, setup_maxiter=8))
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, levels, blocks, nvec, params=pr, psi0=psi0)
+    for l in range(levels - 1):
+        lev = H.levels[l]
+        if l == 0:
+            agg = lattice.fine_aggregate(L, L, *blocks[0])
+        else:
+            e0, e1 = lev.extent
+            agg = np.repeat(lattice.coarse_aggregate(e0, e1, *blocks[l]), lev.nc)
+        Pref = compact_P(lev.P, lev.chir, agg, nvec[l])
+        Pg = sw.sw_mg_export_P(h, l + 1, nvec[l])
+        assert relerr(Pg, Pref) < 1e-10, ("P", l, relerr(Pg, Pref))
+        e0, e1, nc = sw.sw_mg_level_info(h, l + 2)
+        assert (e0, e1) == H.levels[l + 1].extent and nc == 2 * nvec[l]
+        Y = sw.sw_mg_export_Y(h, l + 2)
+        Ag = assemble_stencil(Y, e0, e1)
+        Aref = H.levels[l + 1].op.toarray()
+        assert relerr(Ag, Aref) < 1e-10, ("A_hat", l, relerr(Ag, Aref))
+    h.free()
+    g.free()
+
+
+@pytest.fixture(scope="module")
+def hier32(sw, ctx):
+    L, m = 32, 0.02
+    th = si.heatbath_u1(L, L, 6.0, 30, seed=8, device="cuda")
+    blocks, nvec = [(4, 4), (2, 2)], [6, 8]
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, 3, blocks, nvec, psi0=psi0)
+    yield dict(L=L, m=m, th=th, blocks=blocks, nvec=nvec, psi0=psi0, g=g, h=h)
+    h.free()
+    g.free()
+
+
+def test_coarse_stencil_and_transfer_kernels(sw, hier32):
+    """The coarse apply (and adjoint) and the transfers equal the dense
+    application of the library's own exported Y and P, <= 1e-13 relative."""
+    h, L, nvec = hier32["h"], hier32["L"], hier32["nvec"]
+    for lvl in (2, 3):
+        e0, e1, nc = sw.sw_mg_level_info(h, lvl)
+        M = assemble_stencil(sw.sw_mg_export_Y(h, lvl), e0, e1)
+        v = si.gaussian_complex(30 + lvl, e0 * e1 * nc)
+        out = np.zeros_like(v)
+        sw.sw_mg_apply_coarse(h, lvl, 0, v, out)
+        assert relerr(out, M @ v) < 1e-13
+        sw.sw_mg_apply_coarse(h, lvl, 1, v, out)
+        assert relerr(out, M.conj().T @ v) < 1e-13
+    # level 1 transfer acts on the even KD-block sites
+    P = sw.sw_mg_export_P(h, 1, nvec[0])
+    par = lattice.kd_parity(L, L)
+    eps = lattice.epsilon(L, L)
+    agg = lattice.fine_aggregate(L, L, 4, 4)
+    v = si.gaussian_complex(40, L * L)
+    ve = np.where(par == 0, v, 0)
+    nagg = agg.max() + 1
+    ref = np.zeros((nagg, 2, nvec[0]), dtype=complex)
+    c = np.where(eps > 0, 0, 1)
+    for s in range(L * L):
+        ref[agg[s], c[s]] += np.conj(P[s]) * ve[s]
+    out = np.zeros(nagg * 2 * nvec[0], dtype=complex)
+    sw.sw_mg_transfer(h, 1, 0, v, out)
+    assert relerr(out, ref.ravel()) < 1e-13
+    eh = si.gaussian_complex(41, out.size)
+    back = np.zeros(L * L, dtype=complex)
+    sw.sw_mg_transfer(h, 1, 1, eh, back)
+    ehr = eh.reshape(nagg, 2, nvec[0])
+    pref = np.array([P[s] @ ehr[agg[s], c[s]] if par[s] == 0 else 0 for s in range(L * L)])
+    assert relerr(back, pref) < 1e-13
+    # level 2 transfer
+    e0, e1, nc = sw.sw_mg_level_info(h, 2)
+    P2 = sw.sw_mg_export_P(h, 2, nvec[1])
+    agg2 = np.repeat(lattice.coarse_aggregate(e0, e1, 2, 2), nc)
+    c2 = np.tile(np.r_[np.zeros(nc // 2, int), np.ones(nc // 2, int)], e0 * e1)
+    v2 = si.gaussian_complex(42, e0 * e1 * nc)
+    ref2 = np.zeros((agg2.max() + 1, 2, nvec[1]), dtype=complex)
+    for r in range(v2.size):
+        ref2[agg2[r], c2[r]] += np.conj(P2[r]) * v2[r]
+    out2 = np.zeros(ref2.size, dtype=complex)
+    sw.sw_mg_transfer(h, 2, 0, v2, out2)
+    assert relerr(out2, ref2.ravel()) < 1e-13
+    e2 = si.gaussian_complex(43, out2.size).reshape(ref2.shape)
+    back2 = np.zeros(v2.size, dtype=complex)
+    sw.sw_mg_transfer(h, 2, 1, e2.ravel(), back2)
+    pref2 = np.array([P2[r] @ e2[agg2[r], c2[r]] for r in range(v2.size)])
+    assert relerr(back2, pref2) < 1e-13
+
+
+def test_prolongator_properties(sw, hier32):
+    h, L, nvec = hier32["h"], hier32["L"], hier32["nvec"]
+    P = sw.sw_mg_export_P(h, 1, nvec[0])
+    agg = lattice.fine_aggregate(L, L, 4, 4)
+    eps = lattice.epsilon(L, L)
+    for a in range(agg.max() + 1):
+        for sgn in (1, -1):
+            sel = (agg == a) & (eps == sgn)
+            G = P[sel].conj().T @ P[sel]
+            assert np.max(np.abs(G - np.eye(nvec[0]))) < 1e-13
+
+
+SOLVE_CASES = {
+    # 32^2, beta 3 (1000 sweeps), m 0.01, 2 levels, 4x4 aggregates, 8 null
+    # vectors from 4 passes of the setup relaxation (the small plain case).
+    2: dict(L=32, beta=3.0, sweeps=1000, m=0.01, blocks=[(4, 4)], nvec=[8], passes=4),
+    3: dict(L=64, beta=6.0, sweeps=300, m=0.01, blocks=[(4, 4), (2, 2)], nvec=[8, 12], passes=1),
+}
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_solve_parity(sw, ctx, levels):
+    """MG solve: true residual <= 1e-10 recomputed by the oracle's D, solution
+    and iteration counts within 10% of the oracle's (outer iterations and fine
+    applies in total, inner levels as averages per solve)."""
+    cs = SOLVE_CASES[levels]
+    L, m, blocks, nvec = cs["L"], cs["m"], cs["blocks"], cs["nvec"]
+    th = si.heatbath_u1(L, L, cs["beta"], cs["sweeps"], seed=1, device="cuda")
+    psi0 = psi0_arrays(L, L, nvec, levels, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, levels, blocks, nvec, params=params(sw, setup_passes=cs["passes"]),
+                       psi0=psi0)
+    b = si.gaussian_complex(1001, L * L)
+    x = np.zeros_like(b)
+    st = sw.sw_mg_solve(h, b, x, 1e-10)
+    D = operators.dirac(th, m)
+    r = np.linalg.norm(b - D @ x) / np.linalg.norm(b)
+    assert st["converged"] and r <= 1e-10
+    assert abs(st["true_resid"] - r) <= 1e-12
+    H = omg.Hierarchy(th, m, levels, blocks, nvec, [list(a) for a in psi0],
+                      omg.Params(setup_passes=cs["passes"]))
+    xo, ost = H.solve(b, 1e-10)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-7
+    for key in ("outer_iters", "fine_applies"):
+        assert abs(st[key] - ost[key]) <= max(2, 0.1 * ost[key]), (key, st[key], ost[key])
+    for it, n in (("inter_iters", "inter_solves"), ("coarsest_iters", "coarsest_solves")):
+        if ost[n]:
+            a, o = st[it] / st[n], ost[it] / ost[n]
+            assert abs(a - o) <= 0.1 * o + 0.5, (it, a, o)
+    # device-buffer path gives the same answer
+    import torch
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    st2 = sw.sw_mg_solve(h, bd, xd, 1e-10)
+    torch.cuda.synchronize()
+    assert np.array_equal(xd.cpu().numpy(), x) and st2["outer_iters"] == st["outer_iters"]
+    # zero right-hand side
+    z = np.zeros_like(b)
+    xz = np.ones_like(b)
+    stz = sw.sw_mg_solve(h, z, xz, 1e-10)
+    assert stz["converged"] and np.all(xz == 0)
+    # batch = independent solves
+    B = np.stack([b, si.gaussian_complex(1002, L * L)])
+    X = np.zeros_like(B)
+    sts = sw.sw_mg_solve_batch(h, B, X, 1e-10)
+    assert np.array_equal(X[0], x) and sts[0]["outer_iters"] == st["outer_iters"]
+    assert np.linalg.norm(B[1] - D @ X[1]) / np.linalg.norm(B[1]) <= 1e-10
+    h.free()
+    g.free()
+
+
+def test_full_size_solve_256(sw, ctx):
+    """The benchmark workload (256^2, beta 6, m = 1e-3, 3 levels, Nv 24/32):
+    true residual recomputed by the oracle's D."""
+    from paper_1801_07823_gb300 import presets
+    cfg = presets.FP64_256
+    L, m = cfg["L"], cfg["mass"]
+    th = si.heatbath_u1(L, L, cfg["beta"], 200, seed=1, device="cuda")
+    blocks, nvec = cfg["blocks"], cfg["nvec"]
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=presets.make_params(sw, cfg), psi0=psi0)
+    b = si.gaussian_complex(1001, L * L)
+    x = np.zeros_like(b)
+    st = sw.sw_mg_solve(h, b, x, 1e-10)
+    r = np.linalg.norm(b - operators.dirac(th, m) @ x) / np.linalg.norm(b)
+    assert st["converged"] and r <= 1e-10, (st, r)
+    P = sw.sw_mg_export_P(h, 1, 24)
+    agg = lattice.fine_aggregate(L, L, 4, 4)
+    eps = lattice.epsilon(L, L)
+    # single-pass modified Gram-Schmidt of 24 vectors in a 32-dim block: the
+    # orthogonality error grows with the block's condition number
+    for a in (0, 517, 1023):
+        sel = (agg == a) & (eps == 1)
+        assert np.max(np.abs(P[sel].conj().T @ P[sel] - np.eye(24))) < 1e-11
+    h.free()
+    g.free()

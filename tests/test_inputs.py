@@ -12,6 +12,14 @@ def test_splitmix64_reference_values():
     assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
 
 
+def test_torch_counter_generator_matches_numpy():
+    import torch
+    c = np.arange(0, 5000, 7, dtype=np.uint64)
+    a = si.uniform01(99, c)
+    b = si.torch_uniform01(99, torch.from_numpy(c.astype(np.int64))).numpy()
+    assert np.array_equal(a, b)
+
+
 def test_gaussian_moments():
     z = si.gaussian_complex(12345, 200000)
     assert abs(z.real.mean()) < 0.01 and abs(z.imag.mean()) < 0.01
@@ -30,8 +38,8 @@ def test_heatbath_plaquette_matches_exact_2d_value():
     # volume: <cos theta_p> = I1(beta) / I0(beta).
     from scipy.special import i0, i1
     beta = 6.0
-    vals = [si.plaquette_mean(si.heatbath_u1(32, 32, beta, 60 + 10 * k, seed=11)) for k in range(4)]
-    assert abs(np.mean(vals) - i1(beta) / i0(beta)) < 0.01
+    vals = [si.plaquette_mean(si.heatbath_u1(24, 24, beta, 40 + 10 * k, seed=11)) for k in range(3)]
+    assert abs(np.mean(vals) - i1(beta) / i0(beta)) < 0.015
 
 
 def test_heatbath_deterministic():
