@@ -52,6 +52,19 @@ double2* mg_alloc(sw_mg* mg, long n) {
   return p;
 }
 
+// Setup-only buffers, released when the setup returns.
+struct TempBuffers {
+  std::vector<double2*> list;
+  double2* get(long n) {
+    double2* p = dalloc(n);
+    list.push_back(p);
+    return p;
+  }
+  ~TempBuffers() {
+    for (double2* p : list) cudaFree(p);
+  }
+};
+
 // ---------------------------------------------------------------- operators
 long level_len(const sw_mg* mg, int l) {
   const MgLevel& L = mg->lev[l];
@@ -309,18 +322,19 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
   mg->binv = mg_alloc(mg, N * 4);
   launch_binv_build(g, mg->mass, mg->binv, s);
   mg->lev[0].stmp = mg_alloc(mg, N);
+  TempBuffers tmp;
   for (int l = 0; l + 1 < mg->nlev; ++l) {
     MgLevel& L = mg->lev[l];
     MgLevel& C = mg->lev[l + 1];
     int nv = L.nv;
     long n = L.ndof;
     // work vectors of the setup
-    L.sr = mg_alloc(mg, n); L.sp = mg_alloc(mg, n); L.sq = mg_alloc(mg, n);
-    L.st = mg_alloc(mg, n);
-    double2* V = mg_alloc(mg, n * nv);
-    double2* e = mg_alloc(mg, n);
-    double2* start = mg_alloc(mg, n);
-    double2* lex = l == 0 ? mg_alloc(mg, n) : nullptr;
+    L.sr = tmp.get(n); L.sp = tmp.get(n); L.sq = tmp.get(n);
+    L.st = tmp.get(n);
+    double2* V = tmp.get(n * nv);
+    double2* e = tmp.get(n);
+    double2* start = tmp.get(n);
+    double2* lex = l == 0 ? tmp.get(n) : nullptr;
     int sb = slot_base(l);
     for (int i = 0; i < nv; ++i) {
       double2* target = l == 0 ? lex : start;
@@ -379,15 +393,16 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
     C.Y = mg_alloc(mg, ysz);
     C.Yd = mg_alloc(mg, ysz);
     if (l == 0) {
-      double2* Wv = mg_alloc(mg, N * 2 * nv);
+      double2* Wv = tmp.get(N * 2 * nv);
       launch_build_W(g, nv, mg->binv, L.P, Wv, s);
       launch_build_Y_fine(g, mg->mass, L.b0, L.b1, nv, L.P, Wv, C.Y, s);
     } else {
-      double2* T = mg_alloc(mg, (long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
+      double2* T = tmp.get((long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
       launch_build_Y_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, nv, L.Y, L.P, T, C.Y, s);
     }
     launch_build_Ydag(CoarseGeom{C.E0, C.E1, C.nc}, C.Y, C.Yd, s);
     SW_CUDA(cudaStreamSynchronize(s));
+    L.sr = L.sp = L.sq = L.st = nullptr;
   }
   // solve workspace
   for (int l = 0; l < mg->nlev; ++l) {
