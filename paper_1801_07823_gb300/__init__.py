@@ -20,6 +20,7 @@ __all__ = [
     "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
     "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_coarse", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
+    "sw_dslash_schur_noalloc",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S = 0, 1, 2, 3, 4
@@ -91,6 +92,7 @@ def lib():
             "sw_set_timing": (_I, [_VP, _I]),
             "sw_kernel_times": (_I, [_VP, _I, _VP, _VP]),
             "sw_launch_count": (ctypes.c_longlong, []),
+            "sw_dslash_schur_noalloc": (_I, [_VP, _D, _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -294,3 +296,13 @@ def sw_kernel_times(ctx: _Handle, n: int = 4):
 
 def sw_launch_count() -> int:
     return int(lib().sw_launch_count())
+
+
+def sw_dslash_schur_noalloc(g: _Handle, mass: float, inp, out):
+    """Schur operator with the library's fixed scratch (device tensors only)."""
+    p_in, d_in = _ptr(inp)
+    p_out, d_out = _ptr(out)
+    if not (d_in and d_out):
+        raise ValueError("sw_dslash_schur_noalloc takes device buffers only")
+    _check(lib().sw_dslash_schur_noalloc(g.ptr, float(mass), p_in, p_out), g.ctx_ptr)
+    return out
