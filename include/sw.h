@@ -203,7 +203,10 @@ int sw_dslash_schur_noalloc(sw_gauge* g, double mass, const void* in, void* out)
  *   resets the accumulators.  While enabled, CUDA events recorded on the
  *   context stream bracket every application of a level operator: category 0
  *   = fine Schur operator (3 kernels), category l = coarse stencil of level
- *   l + 1 (1 kernel, also its adjoint).  Synchronises the stream.
+ *   l + 1 (1 kernel, also its adjoint), category 5 = the coarsest-level CGNE
+ *   when it runs as one persistent kernel (one launch per coarsest solve);
+ *   category 6 counts that kernel's CGNE iterations (its ms stay 0).
+ *   Synchronises the stream.
  * sw_kernel_times: for categories 0 .. n-1, the number of applications that
  *   ran and the summed event durations in ms (host arrays, either may be
  *   NULL).  The coarsest solver queues iterations ahead and skips those after
@@ -215,6 +218,12 @@ int sw_dslash_schur_noalloc(sw_gauge* g, double mass, const void* in, void* out)
 int sw_set_timing(sw_ctx* ctx, int enable);
 int sw_kernel_times(sw_ctx* ctx, int n, long long* launches, double* ms);
 long long sw_launch_count(void);
+
+/* Failure-detection check of the persistent coarsest-level CGNE: runs it
+ * once with one CTA withholding its arrival at the first grid barrier, so
+ * every other CTA's bounded wait runs out (about a second).  Expected result:
+ * SW_ERR_TIMEOUT, with the context still usable afterwards. */
+int sw_debug_cgne_stall(sw_mg* mg);
 
 /* SplitMix64 stream seed used when psi0 is NULL (level = index into psi0,
  * 0-based): s1 = mix(seed ^ level) + G, result = mix(s1 ^ index) + G, with

@@ -20,7 +20,7 @@ __all__ = [
     "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
     "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_coarse", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
-    "sw_dslash_schur_noalloc",
+    "sw_dslash_schur_noalloc", "sw_debug_cgne_stall",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S = 0, 1, 2, 3, 4
@@ -93,6 +93,7 @@ def lib():
             "sw_kernel_times": (_I, [_VP, _I, _VP, _VP]),
             "sw_launch_count": (ctypes.c_longlong, []),
             "sw_dslash_schur_noalloc": (_I, [_VP, _D, _VP, _VP]),
+            "sw_debug_cgne_stall": (_I, [_VP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -286,8 +287,9 @@ def sw_set_timing(ctx: _Handle, enable: bool):
     _check(lib().sw_set_timing(ctx.ptr, 1 if enable else 0), ctx.ptr)
 
 
-def sw_kernel_times(ctx: _Handle, n: int = 4):
-    """[(launches, total ms)] per timing category (0: fine S, l: coarse level l+1)."""
+def sw_kernel_times(ctx: _Handle, n: int = 7):
+    """[(launches, total ms)] per timing category (0: fine S, l: coarse level l+1,
+    5: persistent coarsest CGNE kernel, 6: its iteration count)."""
     cnt = np.zeros(n, dtype=np.int64)
     ms = np.zeros(n, dtype=np.float64)
     _check(lib().sw_kernel_times(ctx.ptr, n, cnt.ctypes.data, ms.ctypes.data), ctx.ptr)
@@ -306,3 +308,8 @@ def sw_dslash_schur_noalloc(g: _Handle, mass: float, inp, out):
         raise ValueError("sw_dslash_schur_noalloc takes device buffers only")
     _check(lib().sw_dslash_schur_noalloc(g.ptr, float(mass), p_in, p_out), g.ctx_ptr)
     return out
+
+
+def sw_debug_cgne_stall(mg: _Handle) -> int:
+    """Return code of the persistent CGNE run with a withheld barrier arrival."""
+    return int(lib().sw_debug_cgne_stall(mg.ptr))

@@ -106,7 +106,8 @@ int sw_kernel_times(sw_ctx* c, int n, long long* launches, double* ms) {
     for (int k = 0; k < n && k < kTimeCats; ++k) {
       // category 0 (fine S) is never skipped: count its event pairs; coarse
       // categories count the launches that ran (skipped ones are no-ops)
-      if (launches) launches[k] = k == 0 ? c->t_count[k] : (long long)ex[k];
+      bool host_counted = k == 0 || k >= kCatCgne;
+      if (launches) launches[k] = host_counted ? c->t_count[k] : (long long)ex[k];
       if (ms) ms[k] = c->t_ms[k];
     }
     return SW_OK;
@@ -156,6 +157,8 @@ int sw_context_create(int device, void* cuda_stream, sw_ctx** out) {
     c->counter = dmalloc<unsigned>(1);
     c->flag = dmalloc<int>(1);
     c->ctl = dmalloc<int>(4 * 8);
+    c->bar = dmalloc<unsigned>(2);
+    c->cgstat = dmalloc<int>(4);
     c->exec = dmalloc<unsigned long long>(kTimeCats);
     SW_CUDA(cudaMemset(c->ctl, 0, 4 * 8 * sizeof(int)));
     SW_CUDA(cudaMemset(c->exec, 0, kTimeCats * sizeof(unsigned long long)));
@@ -189,6 +192,8 @@ void sw_context_free(sw_ctx* c) {
   cudaFree(c->flag);
   cudaFree(c->ctl);
   cudaFree(c->exec);
+  cudaFree(c->bar);
+  cudaFree(c->cgstat);
   if (c->h_slots) cudaFreeHost(c->h_slots);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   delete c;
@@ -323,6 +328,8 @@ int sw_mg_setup(sw_gauge* g, double mass, int levels, const int* block, const in
     mg->nlev = levels;
     const char* vb = std::getenv("SW_VERBOSE");
     mg->verbose = vb ? std::atoi(vb) : 0;
+    const char* cl = std::getenv("SW_CGNE_LOOP");
+    mg->persistent_cgne = !(cl && cl[0] == '1');
     if (params)
       mg->p = *params;
     else
@@ -509,7 +516,7 @@ int sw_mg_apply_coarse(sw_mg* mg, int level, int dagger, const void* in, void* o
       din = a;
       dout = b;
     }
-    launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, dagger ? L.Yd : L.Y, din, dout, s);
+    launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, dagger ? 1 : 0, din, dout, s);
     if (!on_device) {
       SW_CUDA(cudaMemcpyAsync(out, dout, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
       SW_CUDA(cudaStreamSynchronize(s));
@@ -561,6 +568,25 @@ int sw_mg_transfer(sw_mg* mg, int level, int dir, const void* in, void* out, int
     cudaFree(b);
     cudaFree(t);
     return SW_OK;
+  });
+}
+
+int sw_debug_cgne_stall(sw_mg* mg) {
+  if (!mg) return SW_ERR_ARG;
+  return guarded(mg->ctx, [&] {
+    const MgLevel& L = mg->lev[mg->nlev - 1];
+    SW_REQUIRE(mg->persistent_cgne, SW_ERR_ARG, "the persistent CGNE is disabled");
+    SW_CUDA(cudaMemsetAsync(L.rhs, 0, L.ndof * sizeof(double2), mg->ctx->stream));
+    mg->stall_test = 1;
+    int rc = SW_OK;
+    try {
+      mg_coarsest_solve(mg, L.rhs, L.sol);
+    } catch (const SwError& e) {
+      mg->stall_test = 0;
+      throw;
+    }
+    mg->stall_test = 0;
+    return rc;
   });
 }
 

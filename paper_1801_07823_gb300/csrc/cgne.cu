@@ -1,0 +1,367 @@
+// Coarsest-level CGNE (CG on the normal error, Sec. IV and Table kcycle) as
+// one persistent cooperative kernel.
+//
+// The coarsest level is small (16^2 sites x 64 dof at 256^2) and its solve
+// runs hundreds of iterations, each two stencil applications and two norms.
+// As separate launches every iteration pays launch latency and a grid tail
+// twice; here all CTAs stay resident, every stencil row is updated where it
+// is computed, and two grid barriers per iteration order the phases:
+//   P1  w = A p (row by row), x += alpha p, r -= alpha w, partial ||r||^2
+//   --- barrier: every CTA adds the partials in the same order -> rr_new;
+//       all CTAs take the same stopping decision
+//   P2  p = A^dag r + beta p (row by row), partial ||p||^2
+//   --- barrier -> pp, alpha = rr_new / pp
+// The per-CTA partials alternate between two arrays, so a CTA that runs ahead
+// never overwrites partials that a slower CTA has still to read.  Work items
+// (site, block of R rows) are dealt to group g of every CTA before group g + 1,
+// so every SM gets the same number of items to within one.
+// A^dag is read from the same stencil storage as A (transposed access), so
+// one copy of the coarsest stencil serves both and stays in L2.
+// The iterates are those of the sequential loop; only the order of the
+// partial sums differs.
+//
+// Barrier waits are bounded: a CTA that waits longer than kSpinLimit polls
+// records an error and every CTA leaves at its next barrier; the host
+// reports SW_ERR_TIMEOUT.
+#include "sw_internal.h"
+
+namespace {
+
+constexpr int kGroups = 4;               // stencil work groups per CTA
+constexpr long kSpinLimit = 1L << 24;    // ~0.3-1.5 s of polling
+
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ int nbr(int X, int d, int E0, int E1) {
+  int X0 = X % E0, X1 = X / E0;
+  if (d == 1) X0 = (X0 + 1 == E0) ? 0 : X0 + 1;
+  if (d == 2) X0 = (X0 == 0) ? E0 - 1 : X0 - 1;
+  if (d == 3) X1 = (X1 + 1 == E1) ? 0 : X1 + 1;
+  if (d == 4) X1 = (X1 == 0) ? E1 - 1 : X1 - 1;
+  return X0 + E0 * X1;
+}
+__device__ __forceinline__ int opp(int d) {
+  return d == 0 ? 0 : (d == 1 ? 2 : (d == 2 ? 1 : (d == 3 ? 4 : 3)));
+}
+
+struct CgneArgs {
+  const double2* Y;
+  const double2* b;
+  double2* x;
+  double2* r;
+  double2* p;
+  double* partials;   // [2][gridDim.x], alternating by phase
+  unsigned* bar;      // [0] arrival count, [1] generation
+  int* status;        // [0] iterations, [1] barrier timeout, [2] non-finite residual
+  int E0, E1, maxit;
+  double tol;
+  int stall_test;     // 1: CTA 0 never arrives at the first barrier (timeout test)
+};
+
+// Grid barrier (all CTAs co-resident: cooperative launch).  Returns false if
+// this CTA gave up waiting or another CTA already did.
+__device__ bool grid_barrier(unsigned* bar, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long spins = 0;
+      while (*gen == g) {
+        if (++spins > kSpinLimit) {
+          atomicExch(status + 1, 1);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok = *((volatile int*)(status + 1)) == 0;
+  }
+  __syncthreads();
+  return ok;
+}
+
+// Sum of one double per CTA (thread 0's value v) into partials[blockIdx.x].
+__device__ void cta_partial(double v, double* red, double* partials) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    partials[blockIdx.x] = s;
+    __threadfence();
+  }
+}
+// Every CTA adds all partials in the same order (lane-strided, then a fixed
+// shuffle tree), so all CTAs hold the same sum.
+__device__ double grid_sum(const double* partials, double* bcast) {
+  if (threadIdx.x < 32) {
+    const volatile double* vp = partials;
+    double s = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s += vp[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *bcast = s;
+  }
+  __syncthreads();
+  return *bcast;
+}
+
+// One row block of the stencil (dagger = 0: A, 1: A^dag) for group item
+// (site X, rows r0 .. r0 + R); result for row i left in part[d == 0 threads].
+template <int NC, int R>
+__device__ __forceinline__ double2 stencil_rows(const double2* __restrict__ Y,
+                                                const double2* __restrict__ v, int X, int r0,
+                                                int d, int ii, int E0, int E1, int dagger,
+                                                double2 (*xs)[NC], double2 (*part)[R],
+                                                int lt, bool active) {
+  if (active)
+    for (int t = lt; t < 5 * NC; t += 5 * R) {
+      int dd = t / NC, j = t - dd * NC;
+      xs[dd][j] = v[(long)nbr(X, dd, E0, E1) * NC + j];
+    }
+  __syncthreads();
+  int i = r0 + ii;
+  double2 acc = make_double2(0.0, 0.0);
+  if (!active) {
+    // a group without an item this round only takes part in the barriers
+  } else if (!dagger) {
+    const double2* y = Y + ((long)X * 5 + d) * NC * NC + i;
+#pragma unroll 16
+    for (int j = 0; j < NC; ++j) cfma(acc, __ldg(y + j * NC), xs[d][j]);
+  } else {
+    int Z = nbr(X, d, E0, E1);
+    const double2* y = Y + (((long)Z * 5 + opp(d)) * NC + i) * NC;
+#pragma unroll 16
+    for (int j = 0; j < NC; ++j) cfmac(acc, __ldg(y + j), xs[d][j]);
+  }
+  part[d][ii] = acc;
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  if (d == 0) {
+    s = part[0][ii];
+#pragma unroll
+    for (int q = 1; q < 5; ++q) {
+      s.x += part[q][ii].x;
+      s.y += part[q][ii].y;
+    }
+  }
+  return s;
+}
+
+template <int NC, int R>
+__global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
+  __shared__ double2 xs_all[kGroups][5][NC];
+  __shared__ double2 part_all[kGroups][5][R];
+  __shared__ double red[32];
+  __shared__ double bcast;
+  const int gsz = 5 * R;
+  int g = threadIdx.x / gsz, lt = threadIdx.x - g * gsz;
+  int d = lt / R, ii = lt - d * R;
+  double2(*xs)[NC] = xs_all[g];
+  double2(*part)[R] = part_all[g];
+  int nsites = a.E0 * a.E1;
+  long n = (long)nsites * NC;
+  int chunks = NC / R;
+  int nitems = nsites * chunks;
+  int ngroups = gridDim.x * kGroups;
+  int rounds = (nitems + ngroups - 1) / ngroups;
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long)gridDim.x * blockDim.x;
+
+  // x = 0, r = b, ||r||^2
+  double acc = 0.0;
+  for (long e = tid; e < n; e += nthr) {
+    double2 v = a.b[e];
+    a.x[e] = make_double2(0.0, 0.0);
+    a.r[e] = v;
+    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+  }
+  // Scalars (stopping test, alpha, beta) are computed once per CTA by thread
+  // 0 from the grid sum and broadcast through shared memory.
+  __shared__ double sh_rr, sh_pp, sh_stop, sh_coef;
+  __shared__ int sh_state;  // 0: continue, 1: converged / cap, 2: non-finite
+  int ph = 0;  // which partials array this phase writes
+  cta_partial(acc, red, a.partials + ph * gridDim.x);
+  if (a.stall_test && blockIdx.x == 0) return;  // the others' first wait must run out
+  if (!grid_barrier(a.bar, a.status)) return;
+  {
+    double rr0 = grid_sum(a.partials + ph * gridDim.x, &bcast);
+    if (threadIdx.x == 0) {
+      sh_rr = rr0;
+      sh_stop = a.tol * sqrt(rr0);
+      sh_state = !isfinite(rr0) ? 2 : ((a.maxit <= 0 || !(sqrt(rr0) > sh_stop)) ? 1 : 0);
+    }
+    __syncthreads();
+  }
+  ph ^= 1;
+  if (sh_state) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.status[0] = 0;
+      if (sh_state == 2) a.status[2] = 1;
+    }
+    return;
+  }
+  // p = A^dag r, ||p||^2
+  acc = 0.0;
+  for (int rd = 0; rd < rounds; ++rd) {
+    int item = rd * ngroups + g * gridDim.x + blockIdx.x;
+    int X = item < nitems ? item / chunks : 0;
+    int r0 = item < nitems ? (item - X * chunks) * R : 0;
+    double2 w = stencil_rows<NC, R>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
+                                    item < nitems);
+    if (d == 0 && item < nitems) {
+      long e = (long)X * NC + r0 + ii;
+      a.p[e] = w;
+      acc = fma(w.x, w.x, fma(w.y, w.y, acc));
+    }
+    __syncthreads();
+  }
+  cta_partial(acc, red, a.partials + ph * gridDim.x);
+  if (!grid_barrier(a.bar, a.status)) return;
+  {
+    double pp = grid_sum(a.partials + ph * gridDim.x, &bcast);
+    if (threadIdx.x == 0) {
+      sh_pp = pp;
+      sh_coef = sh_rr / pp;  // alpha
+    }
+    __syncthreads();
+  }
+  ph ^= 1;
+  int k = 0;
+  for (;;) {
+    double alpha = sh_coef;
+    // P1: w = A p; x += alpha p; r -= alpha w
+    acc = 0.0;
+    for (int rd = 0; rd < rounds; ++rd) {
+      int item = rd * ngroups + g * gridDim.x + blockIdx.x;
+      int X = item < nitems ? item / chunks : 0;
+      int r0 = item < nitems ? (item - X * chunks) * R : 0;
+      double2 w = stencil_rows<NC, R>(a.Y, a.p, X, r0, d, ii, a.E0, a.E1, 0, xs, part, lt,
+                                      item < nitems);
+      if (d == 0 && item < nitems) {
+        long e = (long)X * NC + r0 + ii;
+        double2 pv = a.p[e], xv = a.x[e], rv = a.r[e];
+        xv.x = fma(alpha, pv.x, xv.x);
+        xv.y = fma(alpha, pv.y, xv.y);
+        rv.x = fma(-alpha, w.x, rv.x);
+        rv.y = fma(-alpha, w.y, rv.y);
+        a.x[e] = xv;
+        a.r[e] = rv;
+        acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
+      }
+      __syncthreads();
+    }
+    cta_partial(acc, red, a.partials + ph * gridDim.x);
+    if (!grid_barrier(a.bar, a.status)) return;
+    ++k;
+    {
+      double rr_new = grid_sum(a.partials + ph * gridDim.x, &bcast);
+      if (threadIdx.x == 0) {
+        if (!isfinite(rr_new))
+          sh_state = 2;
+        else if (!(k < a.maxit && sqrt(rr_new) > sh_stop))
+          sh_state = 1;
+        sh_coef = rr_new / sh_rr;  // beta
+        sh_rr = rr_new;
+      }
+      __syncthreads();
+    }
+    ph ^= 1;
+    if (sh_state) break;
+    double beta = sh_coef;
+    // P2: p = A^dag r + beta p
+    acc = 0.0;
+    for (int rd = 0; rd < rounds; ++rd) {
+      int item = rd * ngroups + g * gridDim.x + blockIdx.x;
+      int X = item < nitems ? item / chunks : 0;
+      int r0 = item < nitems ? (item - X * chunks) * R : 0;
+      double2 w = stencil_rows<NC, R>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
+                                      item < nitems);
+      if (d == 0 && item < nitems) {
+        long e = (long)X * NC + r0 + ii;
+        double2 pv = a.p[e];
+        pv.x = fma(beta, pv.x, w.x);
+        pv.y = fma(beta, pv.y, w.y);
+        a.p[e] = pv;
+        acc = fma(pv.x, pv.x, fma(pv.y, pv.y, acc));
+      }
+      __syncthreads();
+    }
+    cta_partial(acc, red, a.partials + ph * gridDim.x);
+    if (!grid_barrier(a.bar, a.status)) return;
+    {
+      double pp = grid_sum(a.partials + ph * gridDim.x, &bcast);
+      if (threadIdx.x == 0) sh_coef = sh_rr / pp;  // alpha
+      __syncthreads();
+    }
+    ph ^= 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.status[0] = k;
+    if (sh_state == 2) a.status[2] = 1;
+  }
+}
+
+template <int NC, int R>
+bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s, int* grid_used) {
+  static int cached_grid[64] = {0};
+  int& grid = cached_grid[device & 63];
+  if (grid == 0) {
+    int occ = 0, sms = 0;
+    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne<NC, R>, kGroups * 5 * R, 0));
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    int coop = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    if (!coop || occ < 1) return false;
+    grid = sms * (occ < 2 ? occ : 2);
+  }
+  CgneArgs a = args;
+  void* params[] = {&a};
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne<NC, R>, dim3(grid),
+                                      dim3(kGroups * 5 * R), params, 0, s));
+  sw_count_launch();
+  *grid_used = grid;
+  return true;
+}
+
+}  // namespace
+
+// Runs the whole coarsest CGNE on the device.  Returns false (nothing
+// launched) when nc has no compiled variant; then the caller uses the
+// host-driven loop.  partials needs 2 x grid doubles (grid <= 2 x SMs), bar 2 unsigned
+// (zeroed here), status 3 ints.
+bool launch_cgne_persistent(const CoarseGeom& g, const double2* Y, const double2* b, double2* x,
+                            double2* r, double2* p, double* partials, unsigned* bar, int* status,
+                            int maxit, double tol, int device, cudaStream_t s, int stall_test) {
+  SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+  SW_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));
+  CgneArgs a{Y, b, x, r, p, partials, bar, status, g.E0, g.E1, maxit, tol, stall_test};
+  int grid = 0;
+  switch (g.nc) {
+    case 16: return launch_cgne_t<16, 8>(a, device, s, &grid);
+    case 24: return launch_cgne_t<24, 8>(a, device, s, &grid);
+    case 32: return launch_cgne_t<32, 16>(a, device, s, &grid);
+    case 48: return launch_cgne_t<48, 16>(a, device, s, &grid);
+    case 64: return launch_cgne_t<64, 16>(a, device, s, &grid);
+    default: return false;
+  }
+}

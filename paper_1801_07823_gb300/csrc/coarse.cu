@@ -6,7 +6,9 @@
 //
 // Stencil storage: Y[X][d] for directions d = 0 (self), 1 (+0hat), 2 (-0hat),
 // 3 (+1hat), 4 (-1hat), each block column-major, element (row i, col j) at
-// ((X * 5 + d) * nc + j) * nc + i.  (A_hat x)_X = sum_d Y[X][d] x_{X+d}.
+// ((X * 5 + d) * nc + j) * nc + i.  (A_hat x)_X = sum_d Y[X][d] x_{X+d}, and
+// the adjoint (A_hat^dag x)_X = sum_d Y[X+d][opp d]^dag x_{X+d} reads the same
+// storage transposed.
 // Direction d collects the couplings carried by fine hops that leave the
 // aggregate in direction d, so the stencil is exact for any coarse extent,
 // including 1 and 2 where X + 0hat and X - 0hat coincide.
@@ -48,7 +50,8 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 // staged in shared memory and every Y load is a coalesced column segment.
 __global__ void k_coarse_apply(const double2* __restrict__ Y, const double2* __restrict__ in,
                                double2* __restrict__ out, int E0, int E1, int nc, int spc,
-                               const int* __restrict__ skip, unsigned long long* exec) {
+                               int dagger, const int* __restrict__ skip,
+                               unsigned long long* exec) {
   extern __shared__ double2 xs[];  // [spc][5][nc]
   if (skip && *skip) return;
   if (exec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(exec, 1ull);
@@ -66,10 +69,17 @@ __global__ void k_coarse_apply(const double2* __restrict__ Y, const double2* __r
   int ls = threadIdx.x / nc, i = threadIdx.x - ls * nc;
   int X = site0 + ls;
   if (ls >= spc || X >= nsites) return;
-  const double2* y = Y + (long)X * 5 * nc * nc + i;
   const double2* xv = xs + ls * 5 * nc;
   double2 acc = make_double2(0.0, 0.0);
-  for (int dj = 0; dj < 5 * nc; ++dj) cfma(acc, __ldg(y + (long)dj * nc), xv[dj]);
+  if (!dagger) {
+    const double2* y = Y + (long)X * 5 * nc * nc + i;
+    for (int dj = 0; dj < 5 * nc; ++dj) cfma(acc, __ldg(y + (long)dj * nc), xv[dj]);
+  } else {
+    for (int d = 0; d < 5; ++d) {
+      const double2* y = Y + (((long)nbr_site(X, d, E0, E1) * 5 + opp_dir(d)) * nc + i) * nc;
+      for (int j = 0; j < nc; ++j) cfmac(acc, __ldg(y + j), xv[d * nc + j]);
+    }
+  }
   out[(long)X * nc + i] = acc;
 }
 
@@ -80,7 +90,7 @@ __global__ void k_coarse_apply(const double2* __restrict__ Y, const double2* __r
 // Y[X][d] (coalesced across i), unrolled so that many loads are in flight:
 // in FP64 the kernel is bound by the FP64 pipe, which needs every SM busy.
 // The five partial sums are added in direction order (deterministic).
-template <int NC>
+template <int NC, bool DAG>
 __global__ void __launch_bounds__(5 * NC) k_coarse_apply_nc(const double2* __restrict__ Y,
                                                             const double2* __restrict__ in,
                                                             double2* __restrict__ out, int E0,
@@ -102,10 +112,19 @@ __global__ void __launch_bounds__(5 * NC) k_coarse_apply_nc(const double2* __res
   __syncthreads();
   int d = threadIdx.x / rows;
   int i = r0 + threadIdx.x - d * rows;
-  const double2* y = Y + ((long)X * 5 + d) * NC * NC + i;
   double2 acc = make_double2(0.0, 0.0);
+  if (!DAG) {
+    const double2* y = Y + ((long)X * 5 + d) * NC * NC + i;
 #pragma unroll 16
-  for (int j = 0; j < NC; ++j) cfma(acc, __ldg(y + j * NC), xs[d][j]);
+    for (int j = 0; j < NC; ++j) cfma(acc, __ldg(y + j * NC), xs[d][j]);
+  } else {
+    // (A^dag)(X, X+d) = Y[X+d][opp d]^dag: row i of it is column i of that
+    // block, contiguous in memory (each thread streams its own column; the
+    // warp's lines are reused from L1 over consecutive j)
+    const double2* y = Y + (((long)nbr_site(X, d, E0, E1) * 5 + opp_dir(d)) * NC + i) * NC;
+#pragma unroll 16
+    for (int j = 0; j < NC; ++j) cfmac(acc, __ldg(y + j), xs[d][j]);
+  }
   part[d][i] = acc;
   __syncthreads();
   if (d == 0) {
@@ -117,25 +136,6 @@ __global__ void __launch_bounds__(5 * NC) k_coarse_apply_nc(const double2* __res
     }
     out[(long)X * NC + i] = s;
   }
-}
-
-// Stencil of the adjoint: (A_hat^dag)(X, X+d) = A_hat(X+d, X)^dag, i.e.
-// Yd[X][d] = Y[X+d][opp(d)]^dag.
-__global__ void k_build_Ydag(const double2* __restrict__ Y, double2* __restrict__ Yd, int E0,
-                             int E1, int nc) {
-  long n = (long)E0 * E1 * 5 * nc * nc;
-  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  int i = (int)(e % nc);
-  long t = e / nc;
-  int j = (int)(t % nc);
-  t /= nc;
-  int d = (int)(t % 5);
-  int X = (int)(t / 5);
-  int Xn = nbr_site(X, d, E0, E1);
-  // Yd[X][d](i, j) = conj(Y[Xn][opp](j, i)); (j, i) sits at col i, row j.
-  double2 v = Y[(((long)Xn * 5 + opp_dir(d)) * nc + i) * nc + j];
-  Yd[e] = make_double2(v.x, -v.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -513,40 +513,41 @@ int pick_spc(int nc) {
 }  // namespace
 
 template <int NC>
-static void coarse_apply_nc(const CoarseGeom& g, const double2* Y, const double2* in, double2* out,
-                            cudaStream_t s, const int* skip, unsigned long long* exec) {
+static void coarse_apply_nc(const CoarseGeom& g, const double2* Y, int dagger, const double2* in,
+                            double2* out, cudaStream_t s, const int* skip,
+                            unsigned long long* exec) {
   int nsites = g.E0 * g.E1;
   // split rows over CTAs until the grid covers the GPU about four times
   int rs = 1;
   while (rs < 8 && NC % (2 * rs) == 0 && (NC / (2 * rs)) % 8 == 0 && (long)nsites * rs < 4 * 152)
     rs *= 2;
-  k_coarse_apply_nc<NC><<<nsites * rs, 5 * (NC / rs), 0, s>>>(Y, in, out, g.E0, g.E1, rs, skip,
-                                                              exec);
+  if (dagger)
+    k_coarse_apply_nc<NC, true><<<nsites * rs, 5 * (NC / rs), 0, s>>>(Y, in, out, g.E0, g.E1, rs,
+                                                                      skip, exec);
+  else
+    k_coarse_apply_nc<NC, false><<<nsites * rs, 5 * (NC / rs), 0, s>>>(Y, in, out, g.E0, g.E1, rs,
+                                                                       skip, exec);
   SW_LAUNCH_CHECK();
 }
 
-void launch_coarse_apply(const CoarseGeom& g, const double2* Y, const double2* in, double2* out,
-                         cudaStream_t s, const int* skip, unsigned long long* exec) {
+void launch_coarse_apply(const CoarseGeom& g, const double2* Y, int dagger, const double2* in,
+                         double2* out, cudaStream_t s, const int* skip,
+                         unsigned long long* exec) {
   switch (g.nc) {
-    case 8: return coarse_apply_nc<8>(g, Y, in, out, s, skip, exec);
-    case 12: return coarse_apply_nc<12>(g, Y, in, out, s, skip, exec);
-    case 16: return coarse_apply_nc<16>(g, Y, in, out, s, skip, exec);
-    case 24: return coarse_apply_nc<24>(g, Y, in, out, s, skip, exec);
-    case 32: return coarse_apply_nc<32>(g, Y, in, out, s, skip, exec);
-    case 48: return coarse_apply_nc<48>(g, Y, in, out, s, skip, exec);
-    case 64: return coarse_apply_nc<64>(g, Y, in, out, s, skip, exec);
+    case 8: return coarse_apply_nc<8>(g, Y, dagger, in, out, s, skip, exec);
+    case 12: return coarse_apply_nc<12>(g, Y, dagger, in, out, s, skip, exec);
+    case 16: return coarse_apply_nc<16>(g, Y, dagger, in, out, s, skip, exec);
+    case 24: return coarse_apply_nc<24>(g, Y, dagger, in, out, s, skip, exec);
+    case 32: return coarse_apply_nc<32>(g, Y, dagger, in, out, s, skip, exec);
+    case 48: return coarse_apply_nc<48>(g, Y, dagger, in, out, s, skip, exec);
+    case 64: return coarse_apply_nc<64>(g, Y, dagger, in, out, s, skip, exec);
     default: break;
   }
   int spc = pick_spc(g.nc);
   int nsites = g.E0 * g.E1;
   size_t smem = (size_t)spc * 5 * g.nc * sizeof(double2);
   k_coarse_apply<<<cdiv(nsites, spc), spc * g.nc, smem, s>>>(Y, in, out, g.E0, g.E1, g.nc, spc,
-                                                              skip, exec);
-  SW_LAUNCH_CHECK();
-}
-void launch_build_Ydag(const CoarseGeom& g, const double2* Y, double2* Yd, cudaStream_t s) {
-  long n = (long)g.E0 * g.E1 * 5 * g.nc * g.nc;
-  k_build_Ydag<<<cdiv(n, 256), 256, 0, s>>>(Y, Yd, g.E0, g.E1, g.nc);
+                                                              dagger, skip, exec);
   SW_LAUNCH_CHECK();
 }
 void launch_restrict_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,

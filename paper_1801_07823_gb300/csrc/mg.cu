@@ -81,7 +81,7 @@ void level_op(sw_mg* mg, int l, const double2* in, double2* out, const int* skip
     mg->st_fine_applies++;
   } else {
     const MgLevel& L = mg->lev[l];
-    launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, in, out, c->stream, skip,
+    launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, 0, in, out, c->stream, skip,
                         c->timing ? c->exec + l : nullptr);
   }
   timing_end(c, tk);
@@ -90,7 +90,7 @@ void level_opdag(sw_mg* mg, int l, const double2* in, double2* out, const int* s
   sw_ctx* c = mg->ctx;
   const MgLevel& L = mg->lev[l];
   int tk = timing_begin(c, l);
-  launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Yd, in, out, c->stream, skip,
+  launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, 1, in, out, c->stream, skip,
                       c->timing ? c->exec + l : nullptr);
   timing_end(c, tk);
 }
@@ -233,6 +233,24 @@ static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
   sw_ctx* c = mg->ctx;
   MgLevel& L = mg->lev[l];
   long n = level_len(mg, l);
+  if (mg->persistent_cgne) {
+    int tk = timing_begin(c, kCatCgne);
+    bool ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, b, x, L.gr, L.cp,
+                                      c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
+                                      mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
+    timing_end(c, tk);
+    if (ran) {
+      SW_CUDA(cudaMemcpyAsync(c->h_ctl, c->cgstat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+      SW_CUDA(cudaStreamSynchronize(c->stream));
+      if (!c->pending.empty()) timing_harvest(c);
+      if (c->timing) c->t_count[kCatCgne + 1] += c->h_ctl[0];  // iterations, for flop counts
+      if (c->h_ctl[1])
+        throw SwError{SW_ERR_TIMEOUT, "coarsest CGNE: a grid barrier wait gave up"};
+      if (c->h_ctl[2]) throw SwError{SW_ERR_NAN, "non-finite norm in CGNE residual"};
+      return c->h_ctl[0];
+    }
+  }
   int sb = slot_base(l);
   int s_rr[2] = {sb + 10, sb + 11}, s_pp = sb + 12;
   int* ctl = c->ctl + 4 * l;
@@ -313,6 +331,10 @@ static int cg_setup(sw_mg* mg, int l, const double2* b, double2* x) {
   return k;
 }
 
+int mg_coarsest_solve(sw_mg* mg, const double2* b, double2* x) {
+  return cgne(mg, mg->nlev - 1, b, x);
+}
+
 // ---------------------------------------------------------------- setup
 void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
   sw_ctx* c = mg->ctx;
@@ -391,7 +413,6 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
     // Galerkin coarse operator and its adjoint stencil
     long ysz = (long)C.E0 * C.E1 * 5 * C.nc * C.nc;
     C.Y = mg_alloc(mg, ysz);
-    C.Yd = mg_alloc(mg, ysz);
     if (l == 0) {
       double2* Wv = tmp.get(N * 2 * nv);
       launch_build_W(g, nv, mg->binv, L.P, Wv, s);
@@ -400,7 +421,6 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
       double2* T = tmp.get((long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
       launch_build_Y_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, nv, L.Y, L.P, T, C.Y, s);
     }
-    launch_build_Ydag(CoarseGeom{C.E0, C.E1, C.nc}, C.Y, C.Yd, s);
     SW_CUDA(cudaStreamSynchronize(s));
     L.sr = L.sp = L.sq = L.st = nullptr;
   }

@@ -67,7 +67,9 @@ constexpr int kNumSlots = 256;
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so every sum has one order
 
 // Per-category kernel timing with CUDA events on the context stream.
-constexpr int kTimeCats = 8;  // 0: fine Schur operator, l: coarse operator of level l + 1
+constexpr int kTimeCats = 8;  // 0: fine Schur operator, l: coarse operator of level l + 1,
+                              // kCatCgne: the persistent coarsest CGNE kernel
+constexpr int kCatCgne = 5;
 struct TimedPair {
   int cat;
   cudaEvent_t a, b;
@@ -89,6 +91,8 @@ struct sw_ctx {
   int* ctl = nullptr;            // device iteration-control blocks, 4 ints per level
   unsigned long long* exec = nullptr;  // device count of executed (not skipped) timed kernels
   int* h_ctl = nullptr;          // pinned host mirror of one control block
+  unsigned* bar = nullptr;       // grid-barrier state of persistent kernels (2 words)
+  int* cgstat = nullptr;         // status words of the persistent CGNE (3 ints)
   double2* h_slots = nullptr;    // pinned host mirror
 };
 
@@ -186,10 +190,16 @@ struct CoarseGeom {
 };
 // skip: optional device flag (see BLAS); exec: optional device counter, bumped
 // once per launch that did run.
-void launch_coarse_apply(const CoarseGeom& g, const double2* Y, const double2* in, double2* out,
-                         cudaStream_t s, const int* skip = nullptr,
+// dagger = 1 applies the adjoint stencil from the same storage.
+void launch_coarse_apply(const CoarseGeom& g, const double2* Y, int dagger, const double2* in,
+                         double2* out, cudaStream_t s, const int* skip = nullptr,
                          unsigned long long* exec = nullptr);
-void launch_build_Ydag(const CoarseGeom& g, const double2* Y, double2* Yd, cudaStream_t s);
+// Whole coarsest-level CGNE in one cooperative launch (cgne.cu); false when nc
+// has no compiled variant.
+bool launch_cgne_persistent(const CoarseGeom& g, const double2* Y, const double2* b, double2* x,
+                            double2* r, double2* p, double* partials, unsigned* bar, int* status,
+                            int maxit, double tol, int device, cudaStream_t s,
+                            int stall_test = 0);
 // Level-1 transfer on the even parity half.  P: [N][nv] parity-split rows.
 void launch_restrict_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,
                           const double2* r_e, double2* out, cudaStream_t s);

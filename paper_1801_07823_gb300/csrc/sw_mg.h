@@ -14,7 +14,6 @@ struct MgLevel {
   int b0 = 0, b1 = 0, nv = 0;
   double2* P = nullptr;   // [ndof][nv]
   double2* Y = nullptr;   // stencil of this level (l > 0), see coarse.cu
-  double2* Yd = nullptr;  // stencil of the adjoint
   // setup work vectors
   double2 *sr = nullptr, *sp = nullptr, *sq = nullptr, *st = nullptr;
   // solve work vectors
@@ -32,6 +31,8 @@ struct sw_mg {
   double mass = 0.0;
   sw_mg_params p{};
   int nlev = 0;
+  int stall_test = 0;  // sw_debug_cgne_stall: make the persistent CGNE's first barrier time out
+  bool persistent_cgne = true;  // SW_CGNE_LOOP=1 selects the host-queued CGNE loop
   int verbose = 0;  // SW_VERBOSE=1: a stderr line per outer iteration; 2: also level 2
   double2* binv = nullptr;
   std::vector<MgLevel> lev;
@@ -48,5 +49,6 @@ inline int slot_base(int l) { return 64 * l; }
 double2* mg_alloc(sw_mg* mg, long n);
 void sw_mg_release(sw_mg* mg);
 void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed);
+int mg_coarsest_solve(sw_mg* mg, const double2* b, double2* x);  // CGNE on the coarsest level
 int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
                     sw_solve_stats* st);

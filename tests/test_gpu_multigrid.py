@@ -235,3 +235,46 @@ def test_full_size_solve_256(sw, ctx):
         assert np.max(np.abs(P[sel].conj().T @ P[sel] - np.eye(24))) < 1e-11
     h.free()
     g.free()
+
+
+def test_persistent_cgne_matches_queued_loop(sw, ctx, monkeypatch):
+    """The one-launch coarsest CGNE and the host-queued loop run the same
+    iteration; their sums run in different orders, so over a whole solve the
+    coarsest counts may drift by roundoff-level stopping decisions (a few per
+    thousand) while the solutions agree to the solve tolerance."""
+    cs = SOLVE_CASES[3]
+    L, m, blocks, nvec = cs["L"], cs["m"], cs["blocks"], cs["nvec"]
+    th = si.heatbath_u1(L, L, cs["beta"], 100, seed=2, device="cuda")
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    b = si.gaussian_complex(1003, L * L)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("SW_CGNE_LOOP", mode)
+        h = sw.sw_mg_setup(g, m, 3, blocks, nvec, psi0=psi0)
+        x = np.zeros_like(b)
+        out[mode] = (sw.sw_mg_solve(h, b, x, 1e-10), x)
+        h.free()
+    (s0, x0), (s1, x1) = out["0"], out["1"]
+    assert abs(s0["coarsest_iters"] - s1["coarsest_iters"]) <= 0.02 * s1["coarsest_iters"]
+    assert abs(s0["outer_iters"] - s1["outer_iters"]) <= 1
+    assert s0["true_resid"] <= 1e-10 and s1["true_resid"] <= 1e-10
+    assert np.linalg.norm(x0 - x1) / np.linalg.norm(x1) < 1e-7
+    g.free()
+
+
+def test_persistent_cgne_barrier_timeout(sw, ctx):
+    """A grid-barrier wait that runs out is reported as SW_ERR_TIMEOUT and the
+    context stays usable (a solve right after succeeds)."""
+    L, m = 32, 0.05
+    th = si.heatbath_u1(L, L, 6.0, 20, seed=3, device="cuda")
+    psi0 = psi0_arrays(L, L, [6, 8], 3, [(4, 4), (2, 2)])
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, 3, [(4, 4), (2, 2)], [6, 8], psi0=psi0)
+    assert sw.sw_debug_cgne_stall(h) == -8
+    b = si.gaussian_complex(5, L * L)
+    x = np.zeros_like(b)
+    st = sw.sw_mg_solve(h, b, x, 1e-10)
+    assert st["converged"] and st["true_resid"] <= 1e-10
+    h.free()
+    g.free()
