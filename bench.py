@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--L", type=int, default=WORKLOAD["L"])
     ap.add_argument("--sweeps", type=int, default=WORKLOAD["sweeps"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the mixed-precision solve measured beside the FP64 one")
     return ap.parse_args()
 
 
@@ -316,6 +318,45 @@ def run_native(args, rank, world, local):
     kern = {names[l]: {"launches": ktimes[l][0], "ms": ktimes[l][1]} for l in names}
     kern["cgne_iterations"] = ktimes[6][0]
 
+    # mixed-precision hierarchy on the same gauge field and right-hand sides:
+    # FP64 outer FGCR, FP32 fine smoother, scaled-FP16 level 2, double-float
+    # coarsest stencil (same timing protocol)
+    variants = {}
+    if not args.no_variants:
+        pm = presets.make_params(sw, presets.FP64_256)
+        pm.precision = sw.SW_MG_MIXED
+        t = time.perf_counter()
+        hm = sw.sw_mg_setup(g, m, 3, WORKLOAD["blocks"], WORKLOAD["nvec"], params=pm, psi0=psi0)
+        msetup = time.perf_counter() - t
+        for k in range(args.warmup):
+            sw.sw_mg_solve(hm, B[k], X, WORKLOAD["tol"])
+        barrier()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        mt = []
+        for k in range(args.warmup, nsteps):
+            flush.zero_()
+            mt.append(sw.sw_mg_solve(hm, B[k], X, WORKLOAD["tol"]))
+        e1_.record(stream)
+        barrier()
+        mel = e0_.elapsed_time(e1_) / 1e3
+        if world > 1:
+            tt = torch.tensor([mel], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            mel = float(tt.item())
+        m0 = mt[0]
+        variants["mixed"] = {
+            "value": world * args.steps / mel, "unit": UNIT, "ms_per_step": mel / args.steps * 1e3,
+            "dtype": "f64 outer FGCR and vectors; f32 fine smoother; f16 (scaled) level-2 "
+                     "stencil; double-float coarsest stencil",
+            "converged_all": all(x_["converged"] and x_["true_resid"] <= WORKLOAD["tol"] for x_ in mt),
+            "true_resid_max": max(x_["true_resid"] for x_ in mt), "setup_s": msetup,
+            "outer_iters": m0["outer_iters"],
+            "inter_avg": m0["inter_iters"] / max(m0["inter_solves"], 1),
+            "coarsest_avg": m0["coarsest_iters"] / max(m0["coarsest_solves"], 1),
+            "speedup_vs_fp64": (world * args.steps / mel) / value}
+        hm.free()
+
     line = None
     if rank == 0:
         cpu = None
@@ -351,6 +392,7 @@ def run_native(args, rank, world, local):
                       "coarsest_avg": s0["coarsest_iters"] / max(s0["coarsest_solves"], 1),
                       "setup_s": setup_s, "wall_s": wall},
             "kernels": kern,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     h.free()

@@ -41,7 +41,12 @@ enum {
 };
 
 enum { SW_OP_D = 0, SW_OP_DDAG = 1, SW_OP_A = 2, SW_OP_ADAG = 3, SW_OP_S = 4 };
-enum { SW_PREC_FP64 = 0, SW_PREC_FP32 = 1 };
+/* Arithmetic of an operator application: FP64; FP32; FP16S = FP16 storage with
+ * one FP32 scale per stencil block and FP32 accumulation; DF64 = double-float
+ * (pairs of FP32 numbers, 48-bit significand) on the FP32 pipes. */
+enum { SW_PREC_FP64 = 0, SW_PREC_FP32 = 1, SW_PREC_FP16S = 2, SW_PREC_DF64 = 3 };
+/* Precision of a multigrid hierarchy (sw_mg_params.precision). */
+enum { SW_MG_FP64 = 0, SW_MG_MIXED = 1 };
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_gauge sw_gauge;
@@ -62,6 +67,13 @@ typedef struct {
   double inter_tol;      /* GCR relative residual on intermediate levels (0.2) */
   int coarsest_maxiter;  /* CGNE iteration cap on the coarsest level (256) */
   double coarsest_tol;   /* CGNE relative residual on the coarsest level (0.2) */
+  int precision;         /* SW_MG_FP64 (default): every operator in FP64.
+                            SW_MG_MIXED: setup, Gram-Schmidt, coarse-operator build,
+                            the outer FGCR (its S, residuals, restarts) and all
+                            vectors and Krylov recurrences stay FP64; inside the
+                            K-cycle the fine S runs in FP32, intermediate-level
+                            stencils in FP16S, and the coarsest CGNE applies its
+                            stencil in DF64. */
 } sw_mg_params;
 
 /* Per-solve counters.  "fine applies" counts applications of the level-1
@@ -166,17 +178,23 @@ int sw_mg_export_P(sw_mg* mg, int level, double* P);
 int sw_mg_export_Y(sw_mg* mg, int level, double* Y);
 
 /* Test access to the level operators and transfers of a hierarchy.
- * sw_mg_apply_coarse: out = A_hat in (dagger = 0) or A_hat^dag in (dagger = 1)
- *   on level l >= 2, vectors [sites][nc] complex128 (Sec. III: A_hat = P^dag A P
- *   applied as the nearest-neighbour stencil of the export above).
+ * sw_mg_apply_level: out = op_l(in).  Level 1: the Schur operator
+ *   I - A_eo A_oe on [L1][L0] complex128 fields (odd-block entries of in
+ *   ignored, of out written 0), precision SW_PREC_FP64, or SW_PREC_FP32 on a
+ *   mixed hierarchy; dagger must be 0.  Level >= 2: the coarse stencil A_hat
+ *   (dagger = 1: A_hat^dag) on [sites][nc] complex128 (Sec. III: A_hat =
+ *   P^dag A P as the nearest-neighbour stencil of the export above) in
+ *   SW_PREC_FP64, or in the reduced copy a mixed hierarchy keeps for that
+ *   level (SW_PREC_FP16S on intermediate levels, SW_PREC_DF64 on the
+ *   coarsest).  Synchronises the stream.
  * sw_mg_transfer: dir = 0 restriction out = P^dag in from level l to l + 1;
  *   dir = 1 prolongation out = P in from level l + 1 to level l.  On level 1
  *   both act on the even KD-block sites only, as inside the solver (Sec. IV:
  *   odd contributions set to zero, odd part of the prolonged error dropped):
  *   odd entries of in are ignored, odd entries of out are written as 0; fine
  *   vectors are [L1][L0]. */
-int sw_mg_apply_coarse(sw_mg* mg, int level, int dagger, const void* in, void* out,
-                       int on_device);
+int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const void* in, void* out,
+                      int on_device);
 int sw_mg_transfer(sw_mg* mg, int level, int dir, const void* in, void* out, int on_device);
 
 /* Schur operator without any device allocation.  The paper has no

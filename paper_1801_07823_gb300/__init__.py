@@ -15,16 +15,18 @@ import numpy as np
 
 __all__ = [
     "SwError", "lib", "SW_OP_D", "SW_OP_DDAG", "SW_OP_A", "SW_OP_ADAG", "SW_OP_S",
-    "SW_PREC_FP64", "SW_PREC_FP32", "sw_context_create", "sw_context_free", "sw_last_error",
+    "SW_PREC_FP64", "SW_PREC_FP32", "SW_PREC_FP16S", "SW_PREC_DF64", "SW_MG_FP64", "SW_MG_MIXED",
+    "sw_context_create", "sw_context_free", "sw_last_error",
     "sw_gauge_load", "sw_gauge_free", "sw_dslash", "sw_mg_params_default", "sw_mg_setup",
     "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
-    "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_coarse", "sw_mg_transfer",
+    "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_level", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
     "sw_dslash_schur_noalloc", "sw_debug_cgne_stall",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S = 0, 1, 2, 3, 4
-SW_PREC_FP64, SW_PREC_FP32 = 0, 1
+SW_PREC_FP64, SW_PREC_FP32, SW_PREC_FP16S, SW_PREC_DF64 = 0, 1, 2, 3
+SW_MG_FP64, SW_MG_MIXED = 0, 1
 ERRORS = {0: "SW_OK", -1: "SW_ERR_ARG", -2: "SW_ERR_SHAPE", -3: "SW_ERR_OOM", -4: "SW_ERR_NOCONV",
           -5: "SW_ERR_BREAKDOWN", -6: "SW_ERR_NAN", -7: "SW_ERR_CUDA", -8: "SW_ERR_TIMEOUT"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsw.so")
@@ -42,7 +44,8 @@ class sw_mg_params(ctypes.Structure):
                 ("outer_maxiter", ctypes.c_int), ("smoother_iters", ctypes.c_int),
                 ("omega", ctypes.c_double), ("inter_restart", ctypes.c_int),
                 ("inter_maxiter", ctypes.c_int), ("inter_tol", ctypes.c_double),
-                ("coarsest_maxiter", ctypes.c_int), ("coarsest_tol", ctypes.c_double)]
+                ("coarsest_maxiter", ctypes.c_int), ("coarsest_tol", ctypes.c_double),
+                ("precision", ctypes.c_int)]
 
 
 class sw_solve_stats(ctypes.Structure):
@@ -86,7 +89,7 @@ def lib():
                                       ctypes.POINTER(_I)]),
             "sw_mg_export_P": (_I, [_VP, _I, _VP]),
             "sw_mg_export_Y": (_I, [_VP, _I, _VP]),
-            "sw_mg_apply_coarse": (_I, [_VP, _I, _I, _VP, _VP, _I]),
+            "sw_mg_apply_level": (_I, [_VP, _I, _I, _I, _VP, _VP, _I]),
             "sw_mg_transfer": (_I, [_VP, _I, _I, _VP, _VP, _I]),
             "sw_stream_seed": (ctypes.c_uint64, [ctypes.c_uint64, _I, _I]),
             "sw_set_timing": (_I, [_VP, _I]),
@@ -265,10 +268,10 @@ def sw_mg_export_Y(mg: _Handle, level: int) -> np.ndarray:
     return Y
 
 
-def sw_mg_apply_coarse(mg: _Handle, level: int, dagger: int, inp, out):
+def sw_mg_apply_level(mg: _Handle, level: int, precision: int, dagger: int, inp, out):
     dev = _same_place(inp, out)
-    _check(lib().sw_mg_apply_coarse(mg.ptr, level, dagger, _ptr(inp)[0], _ptr(out)[0], dev),
-           mg.ctx_ptr)
+    _check(lib().sw_mg_apply_level(mg.ptr, level, precision, dagger, _ptr(inp)[0], _ptr(out)[0],
+                                   dev), mg.ctx_ptr)
     return out
 
 

@@ -14,7 +14,8 @@
 namespace {
 
 __global__ void k_links(const double* __restrict__ theta, double2* __restrict__ Wlex,
-                        float2* __restrict__ Wlex32, double2* __restrict__ Wps, int L0, int L1) {
+                        float2* __restrict__ Wlex32, double2* __restrict__ Wps,
+                        float2* __restrict__ Wps32, int L0, int L1) {
   int N = L0 * L1;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
@@ -29,6 +30,7 @@ __global__ void k_links(const double* __restrict__ theta, double2* __restrict__ 
     Wlex[(long)mu * N + s] = w;
     Wlex32[(long)mu * N + s] = make_float2((float)w.x, (float)w.y);
     Wps[(long)mu * N + f] = w;
+    Wps32[(long)mu * N + f] = make_float2((float)w.x, (float)w.y);
   }
 }
 
@@ -128,6 +130,7 @@ void sw_mg_params_default(sw_mg_params* p) {
   p->inter_tol = 0.2;
   p->coarsest_maxiter = 256;
   p->coarsest_tol = 0.2;
+  p->precision = SW_MG_FP64;
 }
 
 uint64_t sw_stream_seed(uint64_t seed, int level, int index) {
@@ -218,6 +221,7 @@ int sw_gauge_load(sw_ctx* c, int L0, int L1, const double* theta, int on_device,
     g->W_lex = dmalloc<double2>(2 * N);
     g->W_lex32 = dmalloc<float2>(2 * N);
     g->W_ps = dmalloc<double2>(2 * N);
+    g->W_ps32 = dmalloc<float2>(2 * N);
     const double* th = theta;
     double* tmp = nullptr;
     if (!on_device) {
@@ -226,7 +230,7 @@ int sw_gauge_load(sw_ctx* c, int L0, int L1, const double* theta, int on_device,
       th = tmp;
     }
     k_links<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(th, g->W_lex, g->W_lex32, g->W_ps,
-                                                                L0, L1);
+                                                                g->W_ps32, L0, L1);
     SW_LAUNCH_CHECK();
     SW_CUDA(cudaStreamSynchronize(c->stream));
     if (tmp) cudaFree(tmp);
@@ -250,6 +254,7 @@ void sw_gauge_free(sw_gauge* g) {
   cudaFree(g->W_lex);
   cudaFree(g->W_lex32);
   cudaFree(g->W_ps);
+  cudaFree(g->W_ps32);
   cudaFree(g->binv);
   for (auto& t : g->tmp) cudaFree(t);
   delete g;
@@ -335,6 +340,9 @@ int sw_mg_setup(sw_gauge* g, double mass, int levels, const int* block, const in
     else
       sw_mg_params_default(&mg->p);
     const sw_mg_params& p = mg->p;
+    SW_REQUIRE(p.precision == SW_MG_FP64 || p.precision == SW_MG_MIXED, SW_ERR_ARG,
+               "unknown precision");
+    mg->mixed = p.precision == SW_MG_MIXED;
     SW_REQUIRE(p.setup_maxiter >= 0 && p.setup_passes >= 1 && p.outer_restart >= 1 &&
                    p.outer_maxiter >= 0 && p.smoother_iters >= 0 && p.inter_restart >= 1 &&
                    p.inter_maxiter >= 0 && p.coarsest_maxiter >= 0,
@@ -499,32 +507,51 @@ int sw_mg_export_Y(sw_mg* mg, int level, double* Y) {
   });
 }
 
-int sw_mg_apply_coarse(sw_mg* mg, int level, int dagger, const void* in, void* out,
-                       int on_device) {
-  if (!mg || !in || !out || level < 2 || level > mg->nlev) return SW_ERR_ARG;
+int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const void* in, void* out,
+                      int on_device) {
+  if (!mg || !in || !out || level < 1 || level > mg->nlev) return SW_ERR_ARG;
   return guarded(mg->ctx, [&] {
     const MgLevel& L = mg->lev[level - 1];
     cudaStream_t s = mg->ctx->stream;
-    size_t n = L.ndof;
-    const double2* din = (const double2*)in;
-    double2* dout = (double2*)out;
-    double2 *a = nullptr, *b = nullptr;
-    if (!on_device) {
-      a = mg_alloc(mg, n);
-      b = mg_alloc(mg, n);
-      SW_CUDA(cudaMemcpyAsync(a, in, n * sizeof(double2), cudaMemcpyHostToDevice, s));
-      din = a;
-      dout = b;
+    sw_gauge* g = mg->g;
+    size_t n = level == 1 ? (size_t)g->N : (size_t)L.ndof;
+    double2* a = mg_alloc(mg, n);
+    double2* b = mg_alloc(mg, n);
+    double2* t = mg_alloc(mg, n);
+    SW_CUDA(cudaMemcpyAsync(a, in, n * sizeof(double2),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (level == 1) {
+      SW_REQUIRE(!dagger, SW_ERR_ARG, "level 1 has no adjoint here");
+      SW_REQUIRE(precision == SW_PREC_FP64 || (precision == SW_PREC_FP32 && mg->mixed), SW_ERR_ARG,
+                 "level 1: FP64, or FP32 on a mixed-precision hierarchy");
+      launch_pack(g, a, t, s);
+      SW_CUDA(cudaMemsetAsync(a, 0, n * sizeof(double2), s));
+      if (precision == SW_PREC_FP64)
+        fine_apply_S(g, mg->binv, t, a, b, s);
+      else
+        fine_apply_S32(g, g->W_ps32, mg->binv32, t, a, mg->s32tmp, s);
+      launch_unpack(g, a, b, s);
+    } else {
+      CoarseGeom cg{L.E0, L.E1, L.nc};
+      if (precision == SW_PREC_FP64) {
+        launch_coarse_apply(cg, L.Y, dagger ? 1 : 0, a, b, s);
+      } else if (precision == SW_PREC_FP16S) {
+        SW_REQUIRE(L.Yh, SW_ERR_ARG, "no scaled-FP16 stencil on this level");
+        launch_coarse_apply_h(cg, L.Yh, L.Ysc, dagger ? 1 : 0, a, b, s);
+      } else if (precision == SW_PREC_DF64) {
+        SW_REQUIRE(L.Ydf, SW_ERR_ARG, "no double-float stencil on this level");
+        launch_coarse_apply_df(cg, L.Ydf, dagger ? 1 : 0, a, b, s);
+      } else {
+        throw SwError{SW_ERR_ARG, "unknown precision"};
+      }
     }
-    launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, dagger ? 1 : 0, din, dout, s);
-    if (!on_device) {
-      SW_CUDA(cudaMemcpyAsync(out, dout, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      SW_CUDA(cudaStreamSynchronize(s));
-      mg->allocs.pop_back();
-      mg->allocs.pop_back();
-      cudaFree(a);
-      cudaFree(b);
-    }
+    SW_CUDA(cudaMemcpyAsync(out, b, n * sizeof(double2),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    SW_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 3; ++k) mg->allocs.pop_back();
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(t);
     return SW_OK;
   });
 }

@@ -42,6 +42,45 @@ __device__ __forceinline__ void cfmac(double2& acc, double2 a, double2 b) {
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(-a.y, b.x, acc.y);
 }
+// Double-float ("df64") arithmetic on the FP32 pipes (Dekker 1971; Knuth's
+// two-sum): a value is hi + lo with two floats, 48 significant bits.
+// GB300 issues FP32 FMAs at 62x the FP64 rate, so the coarsest stencil in
+// df64 costs about 48 FP32 operations per complex multiply-add instead of 4
+// FP64 FMAs.
+struct df2 {  // accumulator of a real number in df64
+  float hi, lo;
+};
+__device__ __forceinline__ void df_mac(df2& acc, float ah, float al, float bh, float bl) {
+  float p = ah * bh;
+  float e = fmaf(ah, bh, -p);  // exact low part of ah * bh
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);         // al * bl is below the df64 precision
+  float s = acc.hi + p;        // two-sum of acc.hi and p
+  float z = s - acc.hi;
+  float t = (acc.hi - (s - z)) + (p - z);
+  acc.hi = s;
+  acc.lo += t + e;
+}
+__device__ __forceinline__ float4 to_df(double2 v) {  // (re_hi, re_lo, im_hi, im_lo)
+  float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+// acc += a * b (DAG: conj(a) * b) for df64 complex a (stencil entry), b (vector)
+template <bool DAG>
+__device__ __forceinline__ void df_cmac(df2& re, df2& im, float4 a, float4 b) {
+  if (!DAG) {
+    df_mac(re, a.x, a.y, b.x, b.y);
+    df_mac(re, -a.z, -a.w, b.z, b.w);
+    df_mac(im, a.x, a.y, b.z, b.w);
+    df_mac(im, a.z, a.w, b.x, b.y);
+  } else {
+    df_mac(re, a.x, a.y, b.x, b.y);
+    df_mac(re, a.z, a.w, b.z, b.w);
+    df_mac(im, a.x, a.y, b.z, b.w);
+    df_mac(im, -a.z, -a.w, b.x, b.y);
+  }
+}
+
 __device__ __forceinline__ int nbr(int X, int d, int E0, int E1) {
   int X0 = X % E0, X1 = X / E0;
   if (d == 1) X0 = (X0 + 1 == E0) ? 0 : X0 + 1;
@@ -55,7 +94,7 @@ __device__ __forceinline__ int opp(int d) {
 }
 
 struct CgneArgs {
-  const double2* Y;
+  const void* Y;      // complex128 stencil, or df64 float4 stencil for the DF variant
   const double2* b;
   double2* x;
   double2* r;
@@ -127,32 +166,55 @@ __device__ double grid_sum(const double* partials, double* bcast) {
 }
 
 // One row block of the stencil (dagger = 0: A, 1: A^dag) for group item
-// (site X, rows r0 .. r0 + R); result for row i left in part[d == 0 threads].
-template <int NC, int R>
-__device__ __forceinline__ double2 stencil_rows(const double2* __restrict__ Y,
+// (site X, rows r0 .. r0 + R); the row sum is returned to the d == 0 threads.
+// DF: stencil stored as df64 float4, products in df64, vector staged as df64.
+template <int NC, int R, bool DF>
+__device__ __forceinline__ double2 stencil_rows(const void* __restrict__ Yv,
                                                 const double2* __restrict__ v, int X, int r0,
                                                 int d, int ii, int E0, int E1, int dagger,
                                                 double2 (*xs)[NC], double2 (*part)[R],
                                                 int lt, bool active) {
+  float4(*xf)[NC] = reinterpret_cast<float4(*)[NC]>(xs);
   if (active)
     for (int t = lt; t < 5 * NC; t += 5 * R) {
       int dd = t / NC, j = t - dd * NC;
-      xs[dd][j] = v[(long)nbr(X, dd, E0, E1) * NC + j];
+      double2 val = v[(long)nbr(X, dd, E0, E1) * NC + j];
+      if (DF)
+        xf[dd][j] = to_df(val);
+      else
+        xs[dd][j] = val;
     }
   __syncthreads();
   int i = r0 + ii;
   double2 acc = make_double2(0.0, 0.0);
   if (!active) {
     // a group without an item this round only takes part in the barriers
-  } else if (!dagger) {
-    const double2* y = Y + ((long)X * 5 + d) * NC * NC + i;
+  } else if (!DF) {
+    const double2* Y = (const double2*)Yv;
+    if (!dagger) {
+      const double2* y = Y + ((long)X * 5 + d) * NC * NC + i;
 #pragma unroll 16
-    for (int j = 0; j < NC; ++j) cfma(acc, __ldg(y + j * NC), xs[d][j]);
+      for (int j = 0; j < NC; ++j) cfma(acc, __ldg(y + j * NC), xs[d][j]);
+    } else {
+      int Z = nbr(X, d, E0, E1);
+      const double2* y = Y + (((long)Z * 5 + opp(d)) * NC + i) * NC;
+#pragma unroll 16
+      for (int j = 0; j < NC; ++j) cfmac(acc, __ldg(y + j), xs[d][j]);
+    }
   } else {
-    int Z = nbr(X, d, E0, E1);
-    const double2* y = Y + (((long)Z * 5 + opp(d)) * NC + i) * NC;
-#pragma unroll 16
-    for (int j = 0; j < NC; ++j) cfmac(acc, __ldg(y + j), xs[d][j]);
+    const float4* Y = (const float4*)Yv;
+    df2 re{0.f, 0.f}, im{0.f, 0.f};
+    if (!dagger) {
+      const float4* y = Y + ((long)X * 5 + d) * NC * NC + i;
+#pragma unroll 8
+      for (int j = 0; j < NC; ++j) df_cmac<false>(re, im, __ldg(y + j * NC), xf[d][j]);
+    } else {
+      int Z = nbr(X, d, E0, E1);
+      const float4* y = Y + (((long)Z * 5 + opp(d)) * NC + i) * NC;
+#pragma unroll 8
+      for (int j = 0; j < NC; ++j) df_cmac<true>(re, im, __ldg(y + j), xf[d][j]);
+    }
+    acc = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
   }
   part[d][ii] = acc;
   __syncthreads();
@@ -168,7 +230,7 @@ __device__ __forceinline__ double2 stencil_rows(const double2* __restrict__ Y,
   return s;
 }
 
-template <int NC, int R>
+template <int NC, int R, bool DF>
 __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
   __shared__ double2 xs_all[kGroups][5][NC];
   __shared__ double2 part_all[kGroups][5][R];
@@ -226,7 +288,7 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
     int item = rd * ngroups + g * gridDim.x + blockIdx.x;
     int X = item < nitems ? item / chunks : 0;
     int r0 = item < nitems ? (item - X * chunks) * R : 0;
-    double2 w = stencil_rows<NC, R>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
+    double2 w = stencil_rows<NC, R, DF>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
                                     item < nitems);
     if (d == 0 && item < nitems) {
       long e = (long)X * NC + r0 + ii;
@@ -255,7 +317,7 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
       int item = rd * ngroups + g * gridDim.x + blockIdx.x;
       int X = item < nitems ? item / chunks : 0;
       int r0 = item < nitems ? (item - X * chunks) * R : 0;
-      double2 w = stencil_rows<NC, R>(a.Y, a.p, X, r0, d, ii, a.E0, a.E1, 0, xs, part, lt,
+      double2 w = stencil_rows<NC, R, DF>(a.Y, a.p, X, r0, d, ii, a.E0, a.E1, 0, xs, part, lt,
                                       item < nitems);
       if (d == 0 && item < nitems) {
         long e = (long)X * NC + r0 + ii;
@@ -294,7 +356,7 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
       int item = rd * ngroups + g * gridDim.x + blockIdx.x;
       int X = item < nitems ? item / chunks : 0;
       int r0 = item < nitems ? (item - X * chunks) * R : 0;
-      double2 w = stencil_rows<NC, R>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
+      double2 w = stencil_rows<NC, R, DF>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
                                       item < nitems);
       if (d == 0 && item < nitems) {
         long e = (long)X * NC + r0 + ii;
@@ -321,13 +383,14 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
   }
 }
 
-template <int NC, int R>
+template <int NC, int R, bool DF>
 bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s, int* grid_used) {
   static int cached_grid[64] = {0};
   int& grid = cached_grid[device & 63];
   if (grid == 0) {
     int occ = 0, sms = 0;
-    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne<NC, R>, kGroups * 5 * R, 0));
+    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne<NC, R, DF>,
+                                                          kGroups * 5 * R, 0));
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     int coop = 0;
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
@@ -336,32 +399,79 @@ bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s, int* grid_u
   }
   CgneArgs a = args;
   void* params[] = {&a};
-  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne<NC, R>, dim3(grid),
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne<NC, R, DF>, dim3(grid),
                                       dim3(kGroups * 5 * R), params, 0, s));
   sw_count_launch();
   *grid_used = grid;
   return true;
 }
 
+// One double-float stencil application (test access; the solver uses the
+// persistent kernel).  Same per-direction df64 sums as stencil_rows.
+template <bool DAG>
+__global__ void k_coarse_apply_df(const float4* __restrict__ Y, const double2* __restrict__ in,
+                                  double2* __restrict__ out, int E0, int E1, int nc) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)E0 * E1 * nc) return;
+  int X = (int)(e / nc), i = (int)(e - (long)X * nc);
+  double2 tot = make_double2(0.0, 0.0);
+  for (int d = 0; d < 5; ++d) {
+    int Z = nbr(X, d, E0, E1);
+    df2 re{0.f, 0.f}, im{0.f, 0.f};
+    for (int j = 0; j < nc; ++j) {
+      float4 b = to_df(in[(long)Z * nc + j]);
+      if (!DAG)
+        df_cmac<false>(re, im, Y[(((long)X * 5 + d) * nc + j) * nc + i], b);
+      else
+        df_cmac<true>(re, im, Y[(((long)Z * 5 + opp(d)) * nc + i) * nc + j], b);
+    }
+    tot.x += (double)re.hi + (double)re.lo;
+    tot.y += (double)im.hi + (double)im.lo;
+  }
+  out[e] = tot;
+}
+
 }  // namespace
+
+void launch_coarse_apply_df(const CoarseGeom& g, const float4* Y, int dagger, const double2* in,
+                            double2* out, cudaStream_t s) {
+  long n = (long)g.E0 * g.E1 * g.nc;
+  int blocks = (int)((n + 127) / 128);
+  if (dagger)
+    k_coarse_apply_df<true><<<blocks, 128, 0, s>>>(Y, in, out, g.E0, g.E1, g.nc);
+  else
+    k_coarse_apply_df<false><<<blocks, 128, 0, s>>>(Y, in, out, g.E0, g.E1, g.nc);
+  SW_LAUNCH_CHECK();
+}
 
 // Runs the whole coarsest CGNE on the device.  Returns false (nothing
 // launched) when nc has no compiled variant; then the caller uses the
 // host-driven loop.  partials needs 2 x grid doubles (grid <= 2 x SMs), bar 2 unsigned
 // (zeroed here), status 3 ints.
-bool launch_cgne_persistent(const CoarseGeom& g, const double2* Y, const double2* b, double2* x,
-                            double2* r, double2* p, double* partials, unsigned* bar, int* status,
-                            int maxit, double tol, int device, cudaStream_t s, int stall_test) {
+bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const double2* b,
+                            double2* x, double2* r, double2* p, double* partials, unsigned* bar,
+                            int* status, int maxit, double tol, int device, cudaStream_t s,
+                            int stall_test) {
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));
   CgneArgs a{Y, b, x, r, p, partials, bar, status, g.E0, g.E1, maxit, tol, stall_test};
   int grid = 0;
+  if (df64) {
+    switch (g.nc) {
+      case 16: return launch_cgne_t<16, 8, true>(a, device, s, &grid);
+      case 24: return launch_cgne_t<24, 8, true>(a, device, s, &grid);
+      case 32: return launch_cgne_t<32, 16, true>(a, device, s, &grid);
+      case 48: return launch_cgne_t<48, 16, true>(a, device, s, &grid);
+      case 64: return launch_cgne_t<64, 16, true>(a, device, s, &grid);
+      default: return false;
+    }
+  }
   switch (g.nc) {
-    case 16: return launch_cgne_t<16, 8>(a, device, s, &grid);
-    case 24: return launch_cgne_t<24, 8>(a, device, s, &grid);
-    case 32: return launch_cgne_t<32, 16>(a, device, s, &grid);
-    case 48: return launch_cgne_t<48, 16>(a, device, s, &grid);
-    case 64: return launch_cgne_t<64, 16>(a, device, s, &grid);
+    case 16: return launch_cgne_t<16, 8, false>(a, device, s, &grid);
+    case 24: return launch_cgne_t<24, 8, false>(a, device, s, &grid);
+    case 32: return launch_cgne_t<32, 16, false>(a, device, s, &grid);
+    case 48: return launch_cgne_t<48, 16, false>(a, device, s, &grid);
+    case 64: return launch_cgne_t<64, 16, false>(a, device, s, &grid);
     default: return false;
   }
 }

@@ -73,12 +73,21 @@ long level_len(const sw_mg* mg, int l) {
 
 // Operator of level l in the solve: S on level 0 (even half), A_hat below.
 // skip: optional device flag that turns the (coarse) application into a no-op.
-void level_op(sw_mg* mg, int l, const double2* in, double2* out, const int* skip = nullptr) {
+// lowp: inside the preconditioner of a mixed-precision hierarchy -- the fine
+// Schur operator then runs in FP32 and intermediate stencils in scaled FP16.
+void level_op(sw_mg* mg, int l, const double2* in, double2* out, const int* skip = nullptr,
+              bool lowp = false) {
   sw_ctx* c = mg->ctx;
   int tk = timing_begin(c, l);
   if (l == 0) {
-    fine_apply_S(mg->g, mg->binv, in, out, mg->lev[0].stmp, c->stream);
+    if (lowp && mg->mixed)
+      fine_apply_S32(mg->g, mg->g->W_ps32, mg->binv32, in, out, mg->s32tmp, c->stream);
+    else
+      fine_apply_S(mg->g, mg->binv, in, out, mg->lev[0].stmp, c->stream);
     mg->st_fine_applies++;
+  } else if (lowp && mg->mixed && mg->lev[l].Yh) {
+    const MgLevel& L = mg->lev[l];
+    launch_coarse_apply_h(CoarseGeom{L.E0, L.E1, L.nc}, L.Yh, L.Ysc, 0, in, out, c->stream);
   } else {
     const MgLevel& L = mg->lev[l];
     launch_coarse_apply(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, 0, in, out, c->stream, skip,
@@ -114,6 +123,7 @@ static void check_norm(double v, const char* where) {
 // ---------------------------------------------------------------- Krylov
 // MR smoother with zero initial guess: x, r = b - op x.
 static void mr(sw_mg* mg, int l, const double2* b, double2* x, double2* r, double2* q) {
+  const bool lowp = true;  // the smoother always belongs to the preconditioner
   sw_ctx* c = mg->ctx;
   long n = level_len(mg, l);
   int sq = slot_base(l) + 8, sqq = slot_base(l) + 9;
@@ -121,7 +131,7 @@ static void mr(sw_mg* mg, int l, const double2* b, double2* x, double2* r, doubl
   blas_copy(c, r, b, n);
   double om = mg->p.omega;
   for (int it = 0; it < mg->p.smoother_iters; ++it) {
-    level_op(mg, l, r, q);
+    level_op(mg, l, r, q, nullptr, lowp);
     blas_dot(c, q, r, n, sq);
     blas_norm2(c, q, n, sqq);
     blas_axpy(c, x, r, n, coef_ratio(sq, sqq, om));
@@ -148,7 +158,7 @@ static void kcycle(sw_mg* mg, int l, const double2* r, double2* out) {
     launch_prolong_fine(mg->g, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s);
   else
     launch_prolong_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s);
-  level_op(mg, l, L.ke, L.kq);
+  level_op(mg, l, L.ke, L.kq, nullptr, true);
   blas_sub(c, L.kr2, L.kr1, L.kq, n);
   mr(mg, l, L.kr2, L.kx3, L.kr3, L.kq);
   blas_add3(c, out, L.kx1, L.ke, L.kx3, n);
@@ -170,13 +180,14 @@ static GcrResult fgcr(sw_mg* mg, int l, const double2* b, double2* x, double tol
   blas_zero(c, x, n);
   blas_copy(c, L.gr, b, n);
   int k = 0, it = 0, restarts = 0;
+  const bool lowp = l > 0;  // intermediate solves are part of the preconditioner
   for (;;) {
     blas_norm2(c, L.gr, n, s_rr);
     double rn = std::sqrt(slot_read(c, s_rr).x);
     check_norm(rn, "GCR residual");
     if (rn <= tol_abs) {
       if (!confirm) return GcrResult{it, restarts, true};
-      level_op(mg, l, x, L.gtmp);
+      level_op(mg, l, x, L.gtmp, nullptr, lowp);
       blas_sub(c, L.gtmp, b, L.gtmp, n);
       blas_norm2(c, L.gtmp, n, s_rr);
       double rt = std::sqrt(slot_read(c, s_rr).x);
@@ -194,7 +205,7 @@ static GcrResult fgcr(sw_mg* mg, int l, const double2* b, double2* x, double tol
       kcycle(mg, l, L.gr, p);
     else
       blas_copy(c, p, L.gr, n);
-    level_op(mg, l, p, q);
+    level_op(mg, l, p, q, nullptr, lowp);
     for (int j = 0; j < k; ++j) {
       blas_dot(c, L.gq[j], q, n, s_b);
       blas_axpy(c, q, L.gq[j], n, coef_ratio(s_b, -1, -1.0));
@@ -214,7 +225,7 @@ static GcrResult fgcr(sw_mg* mg, int l, const double2* b, double2* x, double tol
                    mg->st_inter_iters, mg->st_inter_solves, mg->st_coarsest_iters,
                    mg->st_coarsest_solves);
     if (k == restart && it < maxiter) {
-      level_op(mg, l, x, L.gtmp);
+      level_op(mg, l, x, L.gtmp, nullptr, lowp);
       blas_sub(c, L.gr, b, L.gtmp, n);
       k = 0;
       ++restarts;
@@ -235,7 +246,10 @@ static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
   long n = level_len(mg, l);
   if (mg->persistent_cgne) {
     int tk = timing_begin(c, kCatCgne);
-    bool ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, L.Y, b, x, L.gr, L.cp,
+    bool df = mg->mixed && L.Ydf;
+    bool ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, df ? (const void*)L.Ydf
+                                                                      : (const void*)L.Y,
+                                      df ? 1 : 0, b, x, L.gr, L.cp,
                                       c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
                                       mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
     timing_end(c, tk);
@@ -344,6 +358,11 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
   mg->binv = mg_alloc(mg, N * 4);
   launch_binv_build(g, mg->mass, mg->binv, s);
   mg->lev[0].stmp = mg_alloc(mg, N);
+  if (mg->mixed) {
+    mg->binv32 = (float2*)mg_alloc(mg, N * 2);
+    launch_to_f32(mg->binv, mg->binv32, N * 4, s);
+    mg->s32tmp = (float2*)mg_alloc(mg, (N + 1) / 2);
+  }
   TempBuffers tmp;
   for (int l = 0; l + 1 < mg->nlev; ++l) {
     MgLevel& L = mg->lev[l];
@@ -420,6 +439,17 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
     } else {
       double2* T = tmp.get((long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
       launch_build_Y_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, nv, L.Y, L.P, T, C.Y, s);
+    }
+    if (mg->mixed) {
+      CoarseGeom cg{C.E0, C.E1, C.nc};
+      if (l + 2 < mg->nlev) {  // intermediate level: scaled FP16 copy
+        C.Yh = (__half2*)mg_alloc(mg, (ysz + 3) / 4);
+        C.Ysc = (float*)mg_alloc(mg, ((long)C.E0 * C.E1 * 5 + 3) / 4);
+        launch_to_half_scaled(cg, C.Y, C.Yh, C.Ysc, s);
+      } else {  // coarsest level: double-float copy
+        C.Ydf = (float4*)mg_alloc(mg, ysz);
+        launch_to_df64(C.Y, C.Ydf, ysz, s);
+      }
     }
     SW_CUDA(cudaStreamSynchronize(s));
     L.sr = L.sp = L.sq = L.st = nullptr;

@@ -1,5 +1,6 @@
 // Internal declarations shared by the translation units of libsw.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -102,6 +103,7 @@ struct sw_gauge {
   double2* W_lex = nullptr;   // [2][N]  W_mu(s) = eta_mu(s) U_mu(s) / 2, site order x0 + L0 x1
   float2* W_lex32 = nullptr;  // FP32 copy for the FP32 Dslash
   double2* W_ps = nullptr;    // [2][N]  same, parity-split block-major order
+  float2* W_ps32 = nullptr;   // FP32 copy of W_ps (mixed-precision Schur operator)
   double binv_mass = -1.0;
   double2* binv = nullptr;    // [N/4][4][4] B^-1 per KD block for binv_mass
   double2* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // [N] scratch for sw_dslash
@@ -196,10 +198,23 @@ void launch_coarse_apply(const CoarseGeom& g, const double2* Y, int dagger, cons
                          unsigned long long* exec = nullptr);
 // Whole coarsest-level CGNE in one cooperative launch (cgne.cu); false when nc
 // has no compiled variant.
-bool launch_cgne_persistent(const CoarseGeom& g, const double2* Y, const double2* b, double2* x,
-                            double2* r, double2* p, double* partials, unsigned* bar, int* status,
-                            int maxit, double tol, int device, cudaStream_t s,
+// Y: complex128 stencil (df64 = 0) or double-float float4 stencil (df64 = 1).
+bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const double2* b,
+                            double2* x, double2* r, double2* p, double* partials, unsigned* bar,
+                            int* status, int maxit, double tol, int device, cudaStream_t s,
                             int stall_test = 0);
+
+// ------------------------------------------------------------- mixed.cu
+void fine_apply_S32(const sw_gauge* g, const float2* W32, const float2* binv32,
+                    const double2* in_e, double2* out_e, float2* tmp, cudaStream_t s);
+void launch_to_f32(const double2* in, float2* out, long n, cudaStream_t s);
+void launch_to_half_scaled(const CoarseGeom& g, const double2* Y, __half2* Yh, float* scale,
+                           cudaStream_t s);
+void launch_coarse_apply_h(const CoarseGeom& g, const __half2* Yh, const float* scale, int dagger,
+                           const double2* in, double2* out, cudaStream_t s);
+void launch_to_df64(const double2* Y, float4* Yd, long n, cudaStream_t s);
+void launch_coarse_apply_df(const CoarseGeom& g, const float4* Y, int dagger, const double2* in,
+                            double2* out, cudaStream_t s);
 // Level-1 transfer on the even parity half.  P: [N][nv] parity-split rows.
 void launch_restrict_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,
                           const double2* r_e, double2* out, cudaStream_t s);

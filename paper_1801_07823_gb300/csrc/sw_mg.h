@@ -14,6 +14,9 @@ struct MgLevel {
   int b0 = 0, b1 = 0, nv = 0;
   double2* P = nullptr;   // [ndof][nv]
   double2* Y = nullptr;   // stencil of this level (l > 0), see coarse.cu
+  __half2* Yh = nullptr;  // mixed precision, intermediate levels: FP16 stencil ...
+  float* Ysc = nullptr;   // ... with one scale per block
+  float4* Ydf = nullptr;  // mixed precision, coarsest level: double-float stencil
   // setup work vectors
   double2 *sr = nullptr, *sp = nullptr, *sq = nullptr, *st = nullptr;
   // solve work vectors
@@ -35,6 +38,9 @@ struct sw_mg {
   bool persistent_cgne = true;  // SW_CGNE_LOOP=1 selects the host-queued CGNE loop
   int verbose = 0;  // SW_VERBOSE=1: a stderr line per outer iteration; 2: also level 2
   double2* binv = nullptr;
+  bool mixed = false;            // params.precision == SW_MG_MIXED
+  float2* binv32 = nullptr;      // FP32 B^-1 (mixed)
+  float2* s32tmp = nullptr;      // [N] FP32 scratch of the FP32 Schur operator
   std::vector<MgLevel> lev;
   std::vector<double2*> allocs;
   double2 *bps = nullptr, *xps = nullptr, *lexb = nullptr, *lexx = nullptr, *lext = nullptr;

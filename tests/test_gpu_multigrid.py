@@ -94,9 +94,9 @@ def test_coarse_stencil_and_transfer_kernels(sw, hier32):
         M = assemble_stencil(sw.sw_mg_export_Y(h, lvl), e0, e1)
         v = si.gaussian_complex(30 + lvl, e0 * e1 * nc)
         out = np.zeros_like(v)
-        sw.sw_mg_apply_coarse(h, lvl, 0, v, out)
+        sw.sw_mg_apply_level(h, lvl, sw.SW_PREC_FP64, 0, v, out)
         assert relerr(out, M @ v) < 1e-13
-        sw.sw_mg_apply_coarse(h, lvl, 1, v, out)
+        sw.sw_mg_apply_level(h, lvl, sw.SW_PREC_FP64, 1, v, out)
         assert relerr(out, M.conj().T @ v) < 1e-13
     # level 1 transfer acts on the even KD-block sites
     P = sw.sw_mg_export_P(h, 1, nvec[0])
@@ -278,3 +278,60 @@ def test_persistent_cgne_barrier_timeout(sw, ctx):
     assert st["converged"] and st["true_resid"] <= 1e-10
     h.free()
     g.free()
+
+
+@pytest.fixture(scope="module")
+def mixed64(sw, ctx):
+    cs = SOLVE_CASES[3]
+    L, m, blocks, nvec = cs["L"], cs["m"], cs["blocks"], cs["nvec"]
+    th = si.heatbath_u1(L, L, cs["beta"], cs["sweeps"], seed=1, device="cuda")
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    h64 = sw.sw_mg_setup(g, m, 3, blocks, nvec, psi0=psi0)
+    hmx = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=params(sw, precision=sw.SW_MG_MIXED),
+                         psi0=psi0)
+    yield dict(L=L, m=m, th=th, g=g, h64=h64, hmx=hmx)
+    hmx.free()
+    h64.free()
+    g.free()
+
+
+def test_mixed_precision_operators(sw, mixed64):
+    """Errors of the reduced-precision operators of a mixed hierarchy: FP32
+    Schur operator against the oracle, scaled-FP16 and double-float stencils
+    against the dense application of the FP64 stencil."""
+    L, m, th, hmx = mixed64["L"], mixed64["m"], mixed64["th"], mixed64["hmx"]
+    F = operators.FineOperators(th, m)
+    v = si.gaussian_complex(50, L * L)
+    ref = np.zeros_like(v)
+    ref[F.even] = F.schur(v[F.even])
+    out = np.zeros_like(v)
+    sw.sw_mg_apply_level(hmx, 1, sw.SW_PREC_FP32, 0, v, out)
+    assert relerr(out, ref) < 2e-6
+    sw.sw_mg_apply_level(hmx, 1, sw.SW_PREC_FP64, 0, v, out)
+    assert relerr(out, ref) < 1e-13
+    for lvl, prec, tol in ((2, sw.SW_PREC_FP16S, 3e-3), (3, sw.SW_PREC_DF64, 1e-12)):
+        e0, e1, nc = sw.sw_mg_level_info(hmx, lvl)
+        M = assemble_stencil(sw.sw_mg_export_Y(hmx, lvl), e0, e1)
+        x = si.gaussian_complex(60 + lvl, e0 * e1 * nc)
+        y = np.zeros_like(x)
+        for dag, Mr in ((0, M), (1, M.conj().T)):
+            sw.sw_mg_apply_level(hmx, lvl, prec, dag, x, y)
+            assert relerr(y, Mr @ x) < tol, (lvl, dag, relerr(y, Mr @ x))
+
+
+def test_mixed_precision_solve(sw, mixed64):
+    """Mixed-precision K-cycle inside an FP64 FGCR reaches the same 1e-10 true
+    residual (recomputed by the oracle's D) with an iteration count close to
+    the FP64 hierarchy's."""
+    L, m, th = mixed64["L"], mixed64["m"], mixed64["th"]
+    b = si.gaussian_complex(1001, L * L)
+    D = operators.dirac(th, m)
+    res = {}
+    for key in ("h64", "hmx"):
+        x = np.zeros_like(b)
+        st = sw.sw_mg_solve(mixed64[key], b, x, 1e-10)
+        r = np.linalg.norm(b - D @ x) / np.linalg.norm(b)
+        assert st["converged"] and r <= 1e-10, (key, r)
+        res[key] = st
+    assert res["hmx"]["outer_iters"] <= res["h64"]["outer_iters"] + 3
