@@ -37,6 +37,17 @@ WORKLOAD = dict(workload="KD-staggered MG solve, 2D U(1) 256x256, beta=6 (2000 h
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 4 FP64 flop/clk/SM (2 DFMA) x 152 SMs x 2070 MHz
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback copy bandwidth
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -143,6 +154,41 @@ def oracle_apply_times(th, m, psi0, reps=5):
         for _ in range(reps):
             op @ v
         out[f"A{l + 1}"] = (time.perf_counter() - t) / reps
+    return out
+
+
+def dslash_bandwidth(sw, ctx, L=4096, reps=20):
+    """Dslash microbenchmark (metric "Dslash GB/s"): D on an L x L lattice, FP64
+    and FP32, timed with CUDA events on the library's stream.  Algorithmic
+    bytes per site: read x (1 complex) and the site's two links, write y;
+    neighbour values and backward links are reused from cache: 64 B (FP64),
+    32 B (FP32).  The working set (>= 1.3 GB) exceeds L2."""
+    import torch
+    gen = torch.Generator(device="cuda").manual_seed(4096)
+    theta = (torch.rand((2, L, L), generator=gen, device="cuda", dtype=torch.float64) * 2 - 1) * math.pi
+    g = sw.sw_gauge_load(ctx, theta)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, prec, dt, bps in (("fp64", sw.SW_PREC_FP64, torch.complex128, 64),
+                                ("fp32", sw.SW_PREC_FP32, torch.complex64, 32)):
+        x = torch.randn(L * L, dtype=dt, device="cuda", generator=gen)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            sw.sw_dslash(g, 0.01, sw.SW_OP_D, prec, x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sw.sw_dslash(g, 0.01, sw.SW_OP_D, prec, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        gbs = bps * L * L / t / 1e9
+        out[name] = {"GB/s": gbs, "frac_of_hbm": gbs / HBM_PEAK_GBS, "us": t * 1e6,
+                     "Gsites/s": L * L / t / 1e9}
+    out["lattice"] = f"{L}x{L}"
+    out["note"] = ("FP64 Dslash issues 20 FP64 operations per site, so on GB300 (4 FP64 flop/clk/SM) "
+                   "it is FP64-ALU bound near 2 TB/s-equivalent; FP32 is HBM bound")
+    g.free()
     return out
 
 
@@ -356,6 +402,24 @@ def run_native(args, rank, world, local):
             "coarsest_avg": m0["coarsest_iters"] / max(m0["coarsest_solves"], 1),
             "speedup_vs_fp64": (world * args.steps / mel) / value}
         hm.free()
+        # the paper's comparison solver on the same system: CG on the even/odd
+        # normal equations (Sec. II, Fig. iterworst), FP64
+        for k in range(1):
+            sw.sw_cg_eo_solve(g, m, B[k], X, WORKLOAD["tol"])
+        barrier()
+        e0_.record(stream)
+        ct = [sw.sw_cg_eo_solve(g, m, B[k], X, WORKLOAD["tol"]) for k in range(args.warmup, nsteps)]
+        e1_.record(stream)
+        barrier()
+        cel = e0_.elapsed_time(e1_) / 1e3
+        variants["cg_eo"] = {
+            "value": world * args.steps / cel, "unit": UNIT, "ms_per_step": cel / args.steps * 1e3,
+            "dtype": "f64", "iterations": ct[0]["outer_iters"],
+            "converged_all": all(x_["converged"] for x_ in ct),
+            "true_resid_max": max(x_["true_resid"] for x_ in ct),
+            "mg_fine_applies_vs_cg": f"{timed[0]['fine_applies']} vs {ct[0]['fine_applies']}"}
+
+    dslash = None if args.no_variants else dslash_bandwidth(sw, ctx)
 
     line = None
     if rank == 0:
@@ -393,6 +457,7 @@ def run_native(args, rank, world, local):
                       "setup_s": setup_s, "wall_s": wall},
             "kernels": kern,
             "variants": variants,
+            "dslash": dslash,
         }
         print(json.dumps(line), flush=True)
     h.free()

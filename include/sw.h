@@ -156,6 +156,17 @@ int sw_mg_solve(sw_mg* mg, const void* b, void* x, double tol, int on_device,
 int sw_mg_solve_batch(sw_mg* mg, int nrhs, const void* B, void* X, double tol, int on_device,
                       sw_solve_stats* st);
 
+/* The paper's comparison solver (Sec. II, Eq. normal; Sec. IV, Fig.
+ * iterworst): CG on the even/odd normal system (m^2 - D_eo D_oe) x_e =
+ * m b_e - D_eo b_o with even/odd = the site parity eps, then
+ * x_o = (b_o - D_oe x_e) / m.  Stops when ||b - D x|| <= tol ||b|| (the CG
+ * residual divided by m) or after maxiter iterations (SW_ERR_NOCONV).
+ * b, x: complex128 [L1][L0].  st (may be NULL): outer_iters = CG iterations,
+ * fine_applies = applications of m^2 - D_eo D_oe, true_resid recomputed.
+ * Allocates its work buffers per call.  Synchronises the stream. */
+int sw_cg_eo_solve(sw_gauge* g, double mass, const void* b, void* x, double tol, int maxiter,
+                   int on_device, sw_solve_stats* st);
+
 /* Integer maps of the lattice and hierarchy, for bit-exact comparison (host
  * buffers of N = L0 L1 int32 each; any may be NULL): eta [2][N] (eta_0, eta_1),
  * eps [N], kd_block [N], kd_parity [N], agg [N] (level-1 aggregate with

@@ -21,7 +21,7 @@ __all__ = [
     "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
     "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_level", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
-    "sw_dslash_schur_noalloc", "sw_debug_cgne_stall",
+    "sw_dslash_schur_noalloc", "sw_debug_cgne_stall", "sw_cg_eo_solve",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S = 0, 1, 2, 3, 4
@@ -97,6 +97,7 @@ def lib():
             "sw_launch_count": (ctypes.c_longlong, []),
             "sw_dslash_schur_noalloc": (_I, [_VP, _D, _VP, _VP]),
             "sw_debug_cgne_stall": (_I, [_VP]),
+            "sw_cg_eo_solve": (_I, [_VP, _D, _VP, _VP, _D, _I, _I, ctypes.POINTER(sw_solve_stats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -316,3 +317,16 @@ def sw_dslash_schur_noalloc(g: _Handle, mass: float, inp, out):
 def sw_debug_cgne_stall(mg: _Handle) -> int:
     """Return code of the persistent CGNE run with a withheld barrier arrival."""
     return int(lib().sw_debug_cgne_stall(mg.ptr))
+
+
+def sw_cg_eo_solve(g: _Handle, mass: float, b, x, tol: float, maxiter: int = 1000000,
+                   allow_noconv: bool = False) -> dict:
+    """CG on the even/odd normal system (the paper's comparison solver)."""
+    dev = _same_place(b, x)
+    st = sw_solve_stats()
+    rc = _check(lib().sw_cg_eo_solve(g.ptr, float(mass), _ptr(b)[0], _ptr(x)[0], float(tol),
+                                     int(maxiter), dev, ctypes.byref(st)), g.ctx_ptr,
+                allow=(-4,) if allow_noconv else ())
+    d = st.as_dict()
+    d["rc"] = rc
+    return d

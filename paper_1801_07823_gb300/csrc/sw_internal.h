@@ -64,7 +64,7 @@ __device__ __forceinline__ double2 coef_eval(const double2* S, Coef c) {
   return v;
 }
 
-constexpr int kNumSlots = 256;
+constexpr int kNumSlots = 320;  // 64 per multigrid level (up to 4), 64 for other solvers
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so every sum has one order
 
 // Per-category kernel timing with CUDA events on the context stream.

@@ -102,3 +102,20 @@ def test_argument_errors(sw, ctx):
         sw.sw_gauge_load(ctx, np.zeros((2, 10, 12)))
     assert e.value.code == -2
     g.free()
+
+
+def test_cg_even_odd_parity(sw, ctx):
+    """The comparison CG on the GPU against the oracle's: same stopping rule,
+    iterations within 3 %, solution within the solve tolerance."""
+    L, m = 64, 0.02
+    th = si.heatbath_u1(L, L, 6.0, 50, seed=9, device="cuda")
+    g = sw.sw_gauge_load(ctx, th)
+    b = si.gaussian_complex(88, L * L)
+    x = np.zeros_like(b)
+    st = sw.sw_cg_eo_solve(g, m, b, x, 1e-10)
+    xo, k = operators.cg_eo_solve(th, m, b, 1e-10, 100000)
+    D = operators.dirac(th, m)
+    assert st["converged"] and np.linalg.norm(b - D @ x) / np.linalg.norm(b) <= 1e-10
+    assert abs(st["outer_iters"] - k) <= max(3, 0.03 * k), (st["outer_iters"], k)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-7
+    g.free()

@@ -243,3 +243,19 @@ def test_maps_of_the_paper():
     for a in range(4):
         assert np.sum(eps[agg == a] == 1) == 32
         assert np.unique(lattice.kd_block(L, L)[agg == a]).size == 16
+
+
+def test_cg_even_odd_solves_the_system():
+    """Sec. II, Eq. normal: D^dag D is block diagonal over the site parity, and
+    CG on m^2 - D_eo D_oe followed by the odd reconstruction solves D x = b."""
+    L, m = 16, 0.05
+    th = rand_theta(L, 31)
+    D = dense_D(th, m)
+    N = D.conj().T @ D
+    eps = lattice.epsilon(L, L)
+    e, o = eps > 0, eps < 0
+    assert np.max(np.abs(N[np.ix_(e, o)])) < 1e-14
+    b = si.gaussian_complex(77, L * L)
+    x, k = operators.cg_eo_solve(th, m, b, 1e-10, 10000)
+    assert np.linalg.norm(b - D @ x) / np.linalg.norm(b) <= 1e-10
+    assert np.max(np.abs(x - np.linalg.solve(D, b))) / np.max(np.abs(x)) < 1e-8
