@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision solve measured beside the FP64 one")
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests of the serving measurement (0: skip it)")
     return ap.parse_args()
 
 
@@ -189,6 +191,47 @@ def dslash_bandwidth(sw, ctx, L=4096, reps=20):
     out["note"] = ("FP64 Dslash issues 20 FP64 operations per site, so on GB300 (4 FP64 flop/clk/SM) "
                    "it is FP64-ALU bound near 2 TB/s-equivalent; FP32 is HBM bound")
     g.free()
+    return out
+
+
+def serving_measurement(nreq, seed=11):
+    """Poisson request stream over 4 resident gauge fields (64^2 and 128^2;
+    beta 6 and 10, 200 heatbath sweeps) with masses log-uniform in [1e-2, 1e-1]
+    served on the mass grid {1e-2, 3e-2, 1e-1}; 2 worker streams;
+    mixed-precision hierarchies with the paper's Table kcycle parameters
+    (Nv 8/12); tol 1e-10.  Latency = finish - arrival, hierarchy setups on first
+    use included."""
+    import sw_inputs as si
+    from paper_1801_07823_gb300 import serve
+    sizes, betas = [64, 128, 64, 128], [6.0, 6.0, 10.0, 10.0]
+    gauges = [(si.heatbath_u1(L, L, b, 200, seed=100 + i, device="cuda"), f"{L}^2 beta={b}")
+              for i, (L, b) in enumerate(zip(sizes, betas))]
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(nreq):
+        gid = int(rng.integers(len(gauges)))
+        L = sizes[gid]
+        m = float(np.exp(rng.uniform(np.log(1e-2), np.log(1e-1))))
+        reqs.append((gid, m, si.gaussian_complex(2000 + i, L * L)))
+    nv = [8, 12]
+
+    def psi0_fn(L):
+        out = [np.stack([si.gaussian_complex(si.stream_seed(5, 0, i), L * L) for i in range(nv[0])])]
+        E = L // 8
+        out.append(np.stack([si.gaussian_complex(si.stream_seed(5, 1, i), E * E * 2 * nv[0])
+                             for i in range(nv[1])]))
+        return out
+
+    srv = serve.Server(gauges, [1e-2, 3e-2, 1e-1], workers=2, hbm_budget=8 << 30,
+                       nvec=tuple(nv), params=dict(outer_maxiter=200), psi0_fn=psi0_fn)
+    done = serve.poisson_stream(srv, reqs, rate=8.0, seed=seed)
+    srv.close()
+    out = serve.latency_summary(done)
+    out["workload"] = ("Poisson arrivals at 8 requests/s; 4 resident gauge fields (64^2, 128^2; "
+                       "beta 6/10, 200 heatbath sweeps); masses log-uniform [1e-2, 1e-1] served on "
+                       "the grid {1e-2, 3e-2, 1e-1}; 2 worker streams; mixed precision, Nv 8/12; "
+                       "hierarchy setups (on first use) count in the latency")
+    out["setups"] = len({(r.worker, r.gauge, r.mass) for r in done})
     return out
 
 
@@ -420,6 +463,9 @@ def run_native(args, rank, world, local):
             "mg_fine_applies_vs_cg": f"{timed[0]['fine_applies']} vs {ct[0]['fine_applies']}"}
 
     dslash = None if args.no_variants else dslash_bandwidth(sw, ctx)
+    serving = None
+    if args.serving_requests > 0 and rank == 0:
+        serving = serving_measurement(args.serving_requests)
 
     line = None
     if rank == 0:
@@ -458,6 +504,7 @@ def run_native(args, rank, world, local):
             "kernels": kern,
             "variants": variants,
             "dslash": dslash,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     h.free()

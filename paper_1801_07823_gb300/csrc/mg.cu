@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "sw_internal.h"
 #include "sw_mg.h"
@@ -240,11 +241,17 @@ static GcrResult fgcr(sw_mg* mg, int l, const double2* b, double2* x, double tol
 // sequential loop: every kernel after the stopping iteration is a no-op.
 constexpr int kIterBatch = 8;
 
+// One persistent (cooperative) kernel at a time per process: two cooperative
+// grids launched from different streams could each hold part of the SMs
+// while waiting at a grid barrier for their own remaining CTAs.
+static std::mutex g_persistent_mutex;
+
 static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
   sw_ctx* c = mg->ctx;
   MgLevel& L = mg->lev[l];
   long n = level_len(mg, l);
   if (mg->persistent_cgne) {
+    std::lock_guard<std::mutex> lock(g_persistent_mutex);  // held until the kernel has finished
     int tk = timing_begin(c, kCatCgne);
     bool df = mg->mixed && L.Ydf;
     bool ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, df ? (const void*)L.Ydf

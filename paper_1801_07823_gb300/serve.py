@@ -1,0 +1,239 @@
+"""Serving loop: a stream of single-RHS solve requests over resident gauge fields.
+
+Requests (gauge field, mass, right-hand side) arrive at any time.  Each worker
+owns one CUDA stream and one libsw context and keeps the multigrid
+hierarchies it has built resident on the device (an LRU cache keyed by gauge
+field and mass).  A request is admitted when a worker is free and its
+hierarchy is cached or fits into the HBM budget (least recently used
+hierarchies of idle workers are evicted to make room); otherwise it waits.
+Admitted requests run concurrently on the workers' streams, so the solves of
+different requests overlap on the GPU while new requests keep arriving
+(continuous admission).  Every kernel of the library sums in a fixed order
+and each context has its own scratch, so a request's result is bitwise the
+same whether it runs alone or in the mix.
+
+Masses are served from a fixed grid (hierarchies are per mass): a request's
+mass is rounded to the nearest grid value on a log scale.
+"""
+from __future__ import annotations
+
+import heapq
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import SW_MG_MIXED, sw_context_create, sw_gauge_load, sw_mg_params_default, sw_mg_setup
+from . import sw_mg_solve
+
+
+def hierarchy_bytes(L: int, blocks, nvec, mixed: bool, outer_restart: int = 32,
+                    inter_restart: int = 8) -> int:
+    """Device bytes of a 3-level (or 2-level) hierarchy and its solve workspace
+    (complex128 = 16 B), from the sizes of its arrays."""
+    N = L * L
+    b = N * 64                                     # B^-1 table
+    b += N * 16 * (4 + 3)                          # fine scratch, lexicographic/parity-split copies
+    b += (N // 2) * 16 * (2 * outer_restart + 13)  # FGCR basis and K-cycle vectors (even half)
+    sites, nc = N, 1
+    E = L
+    for l, (blk, nv) in enumerate(zip(blocks, nvec)):
+        b += sites * nc * nv * 16                  # P
+        E = E // (2 * blk[0]) if l == 0 else E // blk[0]
+        sites, nc = E * E, 2 * nv
+        last = l == len(nvec) - 1
+        ysz = sites * 5 * nc * nc
+        b += ysz * 16                              # Y (FP64)
+        if mixed:
+            b += ysz * (16 if last else 4) + sites * 5 * 4
+        nb = 0 if last else inter_restart
+        b += sites * nc * 16 * (2 * nb + 13)       # solver vectors of this level
+    if mixed:
+        b += N * 32 + N * 8                        # FP32 B^-1 and scratch
+    return int(b)
+
+
+@dataclass(order=True)
+class Request:
+    arrival: float
+    rid: int = field(compare=False)
+    gauge: int = field(compare=False)
+    mass: float = field(compare=False)
+    b: np.ndarray = field(compare=False, repr=False)
+    x: np.ndarray = field(default=None, compare=False, repr=False)
+    start: float = field(default=0.0, compare=False)
+    finish: float = field(default=0.0, compare=False)
+    worker: int = field(default=-1, compare=False)
+    stats: dict = field(default=None, compare=False)
+
+
+class Server:
+    """Multi-worker solve server on one GPU.
+
+    gauges: list of (theta [2, L, L], label).  masses: the mass grid.
+    workers: number of concurrent streams.  hbm_budget: bytes that resident
+    hierarchies may use in total."""
+
+    def __init__(self, gauges, masses, workers=2, hbm_budget=40 << 30, tol=1e-10, mixed=True,
+                 blocks=((4, 4), (2, 2)), nvec=(24, 32), params=None, device=0, psi0_fn=None):
+        import torch
+        self.torch = torch
+        self.gauges = gauges
+        self.masses = np.array(sorted(masses))
+        self.tol = tol
+        self.mixed = mixed
+        self.blocks = [tuple(b) for b in blocks]
+        self.nvec = list(nvec)
+        self.params = params or {}
+        self.budget = hbm_budget
+        self.psi0_fn = psi0_fn
+        self.lock = threading.Condition()
+        self.queue: list[Request] = []
+        self.done: list[Request] = []
+        self.closed = False
+        self.used = 0
+        self.workers = []
+        for w in range(workers):
+            with torch.cuda.device(device):
+                stream = torch.cuda.Stream()
+            ctx = sw_context_create(device, stream.cuda_stream)
+            gh = [sw_gauge_load(ctx, th) for th, _ in gauges]
+            self.workers.append(dict(id=w, stream=stream, ctx=ctx, gauges=gh, cache={},
+                                     busy=False, thread=None))
+        for wk in self.workers:
+            t = threading.Thread(target=self._run, args=(wk,), daemon=True)
+            wk["thread"] = t
+            t.start()
+
+    # ------------------------------------------------------------------ API
+    def snap_mass(self, m: float) -> float:
+        return float(self.masses[np.argmin(np.abs(np.log(self.masses) - np.log(m)))])
+
+    def submit(self, rid: int, gauge: int, mass: float, b: np.ndarray) -> Request:
+        r = Request(time.perf_counter(), rid, gauge, self.snap_mass(mass), b)
+        with self.lock:
+            heapq.heappush(self.queue, r)
+            self.lock.notify_all()
+        return r
+
+    def drain(self):
+        with self.lock:
+            while self.queue or any(w["busy"] for w in self.workers):
+                self.lock.wait(timeout=0.1)
+
+    def close(self):
+        with self.lock:
+            self.closed = True
+            self.lock.notify_all()
+        for wk in self.workers:
+            wk["thread"].join()
+        for wk in self.workers:
+            for h in wk["cache"].values():
+                h["mg"].free()
+            for g in wk["gauges"]:
+                g.free()
+            wk["ctx"].free()
+
+    # ------------------------------------------------------------------ workers
+    def _footprint(self, gauge: int) -> int:
+        L = self.gauges[gauge][0].shape[-1]
+        return hierarchy_bytes(L, self.blocks, self.nvec, self.mixed)
+
+    def _pick(self, wk):
+        """Request this worker serves next (lock held): the earliest one whose
+        hierarchy it already holds, else the earliest one whose hierarchy fits
+        the HBM budget after evicting this worker's least recently used ones."""
+        order = sorted(self.queue)
+        for r in order:
+            if (r.gauge, r.mass) in wk["cache"]:
+                return r, 0
+        for r in order:
+            need = self._footprint(r.gauge)
+            while self.used + need > self.budget and wk["cache"]:
+                k = min(wk["cache"], key=lambda kk: wk["cache"][kk]["last"])
+                h = wk["cache"].pop(k)
+                h["mg"].free()
+                self.used -= h["bytes"]
+            if self.used + need <= self.budget:
+                return r, need
+        return None, 0
+
+    def _run(self, wk):
+        torch = self.torch
+        while True:
+            with self.lock:
+                while True:
+                    if self.closed and not self.queue:
+                        return
+                    r, need = self._pick(wk) if self.queue else (None, 0)
+                    if r is not None:
+                        self.queue = [q for q in self.queue if q is not r]
+                        heapq.heapify(self.queue)
+                        self.used += need
+                        wk["busy"] = True
+                        break
+                    self.lock.wait(timeout=0.05)
+            r.start = time.perf_counter()
+            r.worker = wk["id"]
+            try:
+                with torch.cuda.stream(wk["stream"]):
+                    key = (r.gauge, r.mass)
+                    if key not in wk["cache"]:
+                        p = sw_mg_params_default()
+                        for k, v in self.params.items():
+                            setattr(p, k, v)
+                        if self.mixed:
+                            p.precision = SW_MG_MIXED
+                        L = self.gauges[r.gauge][0].shape[-1]
+                        psi0 = self.psi0_fn(L) if self.psi0_fn else None
+                        try:
+                            mg = sw_mg_setup(wk["gauges"][r.gauge], r.mass, len(self.nvec) + 1,
+                                             self.blocks, self.nvec, params=p, psi0=psi0)
+                        except Exception:
+                            with self.lock:
+                                self.used -= need
+                            raise
+                        wk["cache"][key] = dict(mg=mg, bytes=need, last=0.0)
+                    h = wk["cache"][key]
+                    h["last"] = time.perf_counter()
+                    x = np.zeros_like(r.b)
+                    r.stats = sw_mg_solve(h["mg"], r.b, x, self.tol, allow_noconv=True)
+                    r.x = x
+            except Exception as exc:  # a failed request is reported, the worker goes on
+                r.stats = {"converged": 0, "error": f"{type(exc).__name__}: {exc}"}
+            r.finish = time.perf_counter()
+            with self.lock:
+                wk["busy"] = False
+                self.done.append(r)
+                self.lock.notify_all()
+
+
+def latency_summary(done) -> dict:
+    lat = np.array([r.finish - r.arrival for r in done])
+    if lat.size == 0:
+        return {}
+    span = max(r.finish for r in done) - min(r.arrival for r in done)
+    return {"requests": int(lat.size), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "solves_per_s": float(lat.size / span), "makespan_s": float(span),
+            "all_converged": bool(all(r.stats.get("converged") for r in done)),
+            "failed": int(sum(1 for r in done if not r.stats.get("converged")))}
+
+
+def poisson_stream(server, requests, rate, seed=0):
+    """Submits (gauge, mass, b) requests at Poisson arrival times with the given
+    rate (1/s) and waits until all are done; returns the finished requests.
+    Bound the time of each solve with the server's solver parameters
+    (outer_maxiter)."""
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    t = 0.0
+    for i, (gauge, mass, b) in enumerate(requests):
+        t += rng.exponential(1.0 / rate)
+        delay = t0 + t - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        server.submit(i, gauge, mass, b)
+    server.drain()
+    return sorted(server.done, key=lambda r: r.rid)
