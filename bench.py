@@ -48,6 +48,22 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 
 
+def _profiled_traffic(profile: str, source: str, key: str):
+    """A DRAM-traffic figure recorded in profiles/<profile> by an ncu capture,
+    or None when the kernel source has changed since that capture."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        want = hashlib.sha1(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line)
+    sha = fields.get(f"source_sha1 ({source})")
+    if sha is None or sha.strip() != want or key not in fields:
+        return None
+    return float(fields[key])
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -59,6 +75,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision solve measured beside the FP64 one")
+    ap.add_argument("--dslash-only", action="store_true",
+                    help="run only the Dslash bandwidth microbenchmark")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving measurement (0: skip it)")
     return ap.parse_args()
@@ -396,9 +414,17 @@ def run_native(args, rank, world, local):
         kname = f"k_coarse_apply_nc<{nc}> (level {best + 1}: {e0}x{e1} sites)"
     dur = ms_l / 1e3 / max(n_l, 1)
     achieved = flop / dur / 1e12
+    traffic = None
+    if best == 5:
+        per_iter = _profiled_traffic("k_cgne_fp64_256.md", "paper_1801_07823_gb300/csrc/cgne.cu",
+                                     "dram_bytes_per_iteration")
+        if per_iter is not None:
+            traffic = per_iter * iters / max(n_l, 1)
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "traffic_note": "ncu dram bytes per CGNE iteration (profiles/k_cgne_fp64_256.md) x "
+                            "iterations per launch; null if the kernel changed since",
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 FMA probe: 1.196 "
                            "TFLOP/s at 1995 MHz)",
             "algorithmic_flop_per_launch": flop,
@@ -517,6 +543,14 @@ def run_native(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_init(args)
+    if args.dslash_only:
+        import torch
+        import paper_1801_07823_gb300 as sw
+        torch.cuda.set_device(local)
+        ctx = sw.sw_context_create(local, torch.cuda.current_stream().cuda_stream)
+        print(json.dumps({"dslash": dslash_bandwidth(sw, ctx)}), flush=True)
+        ctx.free()
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
