@@ -11,14 +11,17 @@
 //       all CTAs take the same stopping decision
 //   P2  p = A^dag r + beta p (row by row), partial ||p||^2
 //   --- barrier -> pp, alpha = rr_new / pp
-// The per-CTA partials alternate between two arrays, so a CTA that runs ahead
-// never overwrites partials that a slower CTA has still to read.  Work items
-// (site, block of R rows) are dealt to group g of every CTA before group g + 1,
-// so every SM gets the same number of items to within one.
+// Work items are (site, 8 consecutive rows), one warp each: four lanes share
+// a row, each summing a quarter of the columns of all five blocks, and a
+// fixed shuffle tree adds the quarters, so items need no block-wide barrier.  Items
+// are dealt round-robin over CTAs first, so every SM gets the same number to
+// within one.  The per-CTA partials alternate between two arrays, so a CTA
+// that runs ahead never overwrites partials a slower CTA has still to read.
 // A^dag is read from the same stencil storage as A (transposed access), so
-// one copy of the coarsest stencil serves both and stays in L2.
-// The iterates are those of the sequential loop; only the order of the
-// partial sums differs.
+// one copy of the coarsest stencil serves both and stays in L2.  Vectors
+// written inside the kernel are read with ld.global.cg (L2), never from a
+// possibly stale L1 line.  The iterates are those of the sequential loop;
+// only the order of the partial sums differs.
 //
 // Barrier waits are bounded: a CTA that waits longer than kSpinLimit polls
 // records an error and every CTA leaves at its next barrier; the host
@@ -27,7 +30,6 @@
 
 namespace {
 
-constexpr int kGroups = 4;               // stencil work groups per CTA
 constexpr long kSpinLimit = 1L << 24;    // ~0.3-1.5 s of polling
 
 __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
@@ -99,6 +101,8 @@ struct CgneArgs {
   double2* x;
   double2* r;
   double2* p;
+  float4* rdf;        // DF variant: df64 copies of r and p that the stencil reads
+  float4* pdf;
   double* partials;   // [2][gridDim.x], alternating by phase
   unsigned* bar;      // [0] arrival count, [1] generation
   int* status;        // [0] iterations, [1] barrier timeout, [2] non-finite residual
@@ -138,7 +142,7 @@ __device__ bool grid_barrier(unsigned* bar, int* status) {
   return ok;
 }
 
-// Sum of one double per CTA (thread 0's value v) into partials[blockIdx.x].
+// Sum of one double per thread into partials[blockIdx.x] (fixed order).
 __device__ void cta_partial(double v, double* red, double* partials) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -155,9 +159,8 @@ __device__ void cta_partial(double v, double* red, double* partials) {
 // shuffle tree), so all CTAs hold the same sum.
 __device__ double grid_sum(const double* partials, double* bcast) {
   if (threadIdx.x < 32) {
-    const volatile double* vp = partials;
     double s = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s += vp[q];
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s += __ldcg(partials + q);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) *bcast = s;
   }
@@ -165,89 +168,77 @@ __device__ double grid_sum(const double* partials, double* bcast) {
   return *bcast;
 }
 
-// One row block of the stencil (dagger = 0: A, 1: A^dag) for group item
-// (site X, rows r0 .. r0 + R); the row sum is returned to the d == 0 threads.
-// DF: stencil stored as df64 float4, products in df64, vector staged as df64.
-template <int NC, int R, bool DF>
-__device__ __forceinline__ double2 stencil_rows(const void* __restrict__ Yv,
-                                                const double2* __restrict__ v, int X, int r0,
-                                                int d, int ii, int E0, int E1, int dagger,
-                                                double2 (*xs)[NC], double2 (*part)[R],
-                                                int lt, bool active) {
-  float4(*xf)[NC] = reinterpret_cast<float4(*)[NC]>(xs);
-  if (active)
-    for (int t = lt; t < 5 * NC; t += 5 * R) {
-      int dd = t / NC, j = t - dd * NC;
-      double2 val = v[(long)nbr(X, dd, E0, E1) * NC + j];
-      if (DF)
-        xf[dd][j] = to_df(val);
-      else
-        xs[dd][j] = val;
-    }
-  __syncthreads();
-  int i = r0 + ii;
+constexpr int kWarps = 8;  // warps per CTA
+constexpr int kRows = 8;   // rows per work item (one warp, 4 lanes per row)
+
+// Row i of (A v)_X (dagger: (A^dag v)_X) summed by the 4 lanes of the row:
+// lane q takes columns j in [q nc/4, (q+1) nc/4) of all five blocks.  Every
+// lane of the row returns the same value.
+template <int NC, bool DF>
+__device__ __forceinline__ double2 stencil_row(const void* __restrict__ Yv,
+                                               const double2* __restrict__ v,
+                                               const float4* __restrict__ vdf, int X, int i,
+                                               int q, int E0, int E1, bool dagger) {
+  constexpr int QJ = NC / 4;  // columns per lane and direction
+  const int j0 = q * QJ;
   double2 acc = make_double2(0.0, 0.0);
-  if (!active) {
-    // a group without an item this round only takes part in the barriers
-  } else if (!DF) {
-    const double2* Y = (const double2*)Yv;
-    if (!dagger) {
-      const double2* y = Y + ((long)X * 5 + d) * NC * NC + i;
-#pragma unroll 16
-      for (int j = 0; j < NC; ++j) cfma(acc, __ldg(y + j * NC), xs[d][j]);
-    } else {
-      int Z = nbr(X, d, E0, E1);
-      const double2* y = Y + (((long)Z * 5 + opp(d)) * NC + i) * NC;
-#pragma unroll 16
-      for (int j = 0; j < NC; ++j) cfmac(acc, __ldg(y + j), xs[d][j]);
-    }
-  } else {
-    const float4* Y = (const float4*)Yv;
-    df2 re{0.f, 0.f}, im{0.f, 0.f};
-    if (!dagger) {
-      const float4* y = Y + ((long)X * 5 + d) * NC * NC + i;
-#pragma unroll 8
-      for (int j = 0; j < NC; ++j) df_cmac<false>(re, im, __ldg(y + j * NC), xf[d][j]);
-    } else {
-      int Z = nbr(X, d, E0, E1);
-      const float4* y = Y + (((long)Z * 5 + opp(d)) * NC + i) * NC;
-#pragma unroll 8
-      for (int j = 0; j < NC; ++j) df_cmac<true>(re, im, __ldg(y + j), xf[d][j]);
-    }
-    acc = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
-  }
-  part[d][ii] = acc;
-  __syncthreads();
-  double2 s = make_double2(0.0, 0.0);
-  if (d == 0) {
-    s = part[0][ii];
+  df2 re{0.f, 0.f}, im{0.f, 0.f};
 #pragma unroll
-    for (int q = 1; q < 5; ++q) {
-      s.x += part[q][ii].x;
-      s.y += part[q][ii].y;
+  for (int d = 0; d < 5; ++d) {
+    const long nb = nbr(X, d, E0, E1);
+    const long ybase = dagger ? ((nb * 5 + opp(d)) * NC + i) * NC + j0
+                              : (((long)X * 5 + d) * NC + j0) * NC + i;
+    const long ystep = dagger ? 1 : NC;
+    const long xbase = nb * NC + j0;
+    if (!DF) {
+      const double2* Y = (const double2*)Yv + ybase;
+#pragma unroll 8
+      for (int t = 0; t < QJ; ++t) {
+        double2 y = __ldg(Y + t * ystep);
+        double2 xv = __ldcg(v + xbase + t);
+        if (dagger)
+          cfmac(acc, y, xv);
+        else
+          cfma(acc, y, xv);
+      }
+    } else {
+      const float4* Y = (const float4*)Yv + ybase;
+#pragma unroll 8
+      for (int t = 0; t < QJ; ++t) {
+        float4 y = __ldg(Y + t * ystep);
+        float4 xv = __ldcg(vdf + xbase + t);
+        if (dagger)
+          df_cmac<true>(re, im, y, xv);
+        else
+          df_cmac<false>(re, im, y, xv);
+      }
     }
   }
-  return s;
+  if (DF) acc = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+  // quarters of the row: butterfly over lanes q = 0..3 (exactly commutative)
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+  return acc;
 }
 
-template <int NC, int R, bool DF>
-__global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
-  __shared__ double2 xs_all[kGroups][5][NC];
-  __shared__ double2 part_all[kGroups][5][R];
+template <int NC, bool DF>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_cgne(CgneArgs a) {
   __shared__ double red[32];
   __shared__ double bcast;
-  const int gsz = 5 * R;
-  int g = threadIdx.x / gsz, lt = threadIdx.x - g * gsz;
-  int d = lt / R, ii = lt - d * R;
-  double2(*xs)[NC] = xs_all[g];
-  double2(*part)[R] = part_all[g];
-  int nsites = a.E0 * a.E1;
-  long n = (long)nsites * NC;
-  int chunks = NC / R;
-  int nitems = nsites * chunks;
-  int ngroups = gridDim.x * kGroups;
-  int rounds = (nitems + ngroups - 1) / ngroups;
-  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long)gridDim.x * blockDim.x;
+  __shared__ double sh_rr, sh_stop, sh_coef;
+  __shared__ int sh_state;  // 0: continue, 1: converged / cap, 2: non-finite
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rr8 = lane >> 2, q = lane & 3;
+  const int nsites = a.E0 * a.E1;
+  const long n = (long)nsites * NC;
+  const int chunks = NC / kRows;
+  const int nitems = nsites * chunks;
+  const int nwarps = gridDim.x * kWarps;
+  const int rounds = (nitems + nwarps - 1) / nwarps;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nthr = (long)gridDim.x * blockDim.x;
 
   // x = 0, r = b, ||r||^2
   double acc = 0.0;
@@ -255,12 +246,9 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
     double2 v = a.b[e];
     a.x[e] = make_double2(0.0, 0.0);
     a.r[e] = v;
+    if (DF) a.rdf[e] = to_df(v);
     acc = fma(v.x, v.x, fma(v.y, v.y, acc));
   }
-  // Scalars (stopping test, alpha, beta) are computed once per CTA by thread
-  // 0 from the grid sum and broadcast through shared memory.
-  __shared__ double sh_rr, sh_pp, sh_stop, sh_coef;
-  __shared__ int sh_state;  // 0: continue, 1: converged / cap, 2: non-finite
   int ph = 0;  // which partials array this phase writes
   cta_partial(acc, red, a.partials + ph * gridDim.x);
   if (a.stall_test && blockIdx.x == 0) return;  // the others' first wait must run out
@@ -285,26 +273,22 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
   // p = A^dag r, ||p||^2
   acc = 0.0;
   for (int rd = 0; rd < rounds; ++rd) {
-    int item = rd * ngroups + g * gridDim.x + blockIdx.x;
-    int X = item < nitems ? item / chunks : 0;
-    int r0 = item < nitems ? (item - X * chunks) * R : 0;
-    double2 w = stencil_rows<NC, R, DF>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
-                                    item < nitems);
-    if (d == 0 && item < nitems) {
-      long e = (long)X * NC + r0 + ii;
+    int item = rd * nwarps + warp * gridDim.x + blockIdx.x;
+    if (item >= nitems) break;  // warp-uniform
+    int X = item / chunks, i = (item - X * chunks) * kRows + rr8;
+    double2 w = stencil_row<NC, DF>(a.Y, a.r, a.rdf, X, i, q, a.E0, a.E1, true);
+    if (q == 0) {
+      long e = (long)X * NC + i;
       a.p[e] = w;
+      if (DF) a.pdf[e] = to_df(w);
       acc = fma(w.x, w.x, fma(w.y, w.y, acc));
     }
-    __syncthreads();
   }
   cta_partial(acc, red, a.partials + ph * gridDim.x);
   if (!grid_barrier(a.bar, a.status)) return;
   {
     double pp = grid_sum(a.partials + ph * gridDim.x, &bcast);
-    if (threadIdx.x == 0) {
-      sh_pp = pp;
-      sh_coef = sh_rr / pp;  // alpha
-    }
+    if (threadIdx.x == 0) sh_coef = sh_rr / pp;  // alpha
     __syncthreads();
   }
   ph ^= 1;
@@ -314,23 +298,22 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
     // P1: w = A p; x += alpha p; r -= alpha w
     acc = 0.0;
     for (int rd = 0; rd < rounds; ++rd) {
-      int item = rd * ngroups + g * gridDim.x + blockIdx.x;
-      int X = item < nitems ? item / chunks : 0;
-      int r0 = item < nitems ? (item - X * chunks) * R : 0;
-      double2 w = stencil_rows<NC, R, DF>(a.Y, a.p, X, r0, d, ii, a.E0, a.E1, 0, xs, part, lt,
-                                      item < nitems);
-      if (d == 0 && item < nitems) {
-        long e = (long)X * NC + r0 + ii;
-        double2 pv = a.p[e], xv = a.x[e], rv = a.r[e];
+      int item = rd * nwarps + warp * gridDim.x + blockIdx.x;
+      if (item >= nitems) break;
+      int X = item / chunks, i = (item - X * chunks) * kRows + rr8;
+      double2 w = stencil_row<NC, DF>(a.Y, a.p, a.pdf, X, i, q, a.E0, a.E1, false);
+      if (q == 0) {
+        long e = (long)X * NC + i;
+        double2 pv = __ldcg(a.p + e), xv = __ldcg(a.x + e), rv = __ldcg(a.r + e);
         xv.x = fma(alpha, pv.x, xv.x);
         xv.y = fma(alpha, pv.y, xv.y);
         rv.x = fma(-alpha, w.x, rv.x);
         rv.y = fma(-alpha, w.y, rv.y);
         a.x[e] = xv;
         a.r[e] = rv;
+        if (DF) a.rdf[e] = to_df(rv);
         acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
       }
-      __syncthreads();
     }
     cta_partial(acc, red, a.partials + ph * gridDim.x);
     if (!grid_barrier(a.bar, a.status)) return;
@@ -353,20 +336,19 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
     // P2: p = A^dag r + beta p
     acc = 0.0;
     for (int rd = 0; rd < rounds; ++rd) {
-      int item = rd * ngroups + g * gridDim.x + blockIdx.x;
-      int X = item < nitems ? item / chunks : 0;
-      int r0 = item < nitems ? (item - X * chunks) * R : 0;
-      double2 w = stencil_rows<NC, R, DF>(a.Y, a.r, X, r0, d, ii, a.E0, a.E1, 1, xs, part, lt,
-                                      item < nitems);
-      if (d == 0 && item < nitems) {
-        long e = (long)X * NC + r0 + ii;
-        double2 pv = a.p[e];
+      int item = rd * nwarps + warp * gridDim.x + blockIdx.x;
+      if (item >= nitems) break;
+      int X = item / chunks, i = (item - X * chunks) * kRows + rr8;
+      double2 w = stencil_row<NC, DF>(a.Y, a.r, a.rdf, X, i, q, a.E0, a.E1, true);
+      if (q == 0) {
+        long e = (long)X * NC + i;
+        double2 pv = __ldcg(a.p + e);
         pv.x = fma(beta, pv.x, w.x);
         pv.y = fma(beta, pv.y, w.y);
         a.p[e] = pv;
+        if (DF) a.pdf[e] = to_df(pv);
         acc = fma(pv.x, pv.x, fma(pv.y, pv.y, acc));
       }
-      __syncthreads();
     }
     cta_partial(acc, red, a.partials + ph * gridDim.x);
     if (!grid_barrier(a.bar, a.status)) return;
@@ -383,31 +365,8 @@ __global__ void __launch_bounds__(kGroups * 5 * R) k_cgne(CgneArgs a) {
   }
 }
 
-template <int NC, int R, bool DF>
-bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s, int* grid_used) {
-  static int cached_grid[64] = {0};
-  int& grid = cached_grid[device & 63];
-  if (grid == 0) {
-    int occ = 0, sms = 0;
-    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne<NC, R, DF>,
-                                                          kGroups * 5 * R, 0));
-    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-    int coop = 0;
-    SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
-    if (!coop || occ < 1) return false;
-    grid = sms * (occ < 2 ? occ : 2);
-  }
-  CgneArgs a = args;
-  void* params[] = {&a};
-  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne<NC, R, DF>, dim3(grid),
-                                      dim3(kGroups * 5 * R), params, 0, s));
-  sw_count_launch();
-  *grid_used = grid;
-  return true;
-}
-
 // One double-float stencil application (test access; the solver uses the
-// persistent kernel).  Same per-direction df64 sums as stencil_rows.
+// persistent kernel); df64 sums per direction, added in FP64.
 template <bool DAG>
 __global__ void k_coarse_apply_df(const float4* __restrict__ Y, const double2* __restrict__ in,
                                   double2* __restrict__ out, int E0, int E1, int nc) {
@@ -431,6 +390,27 @@ __global__ void k_coarse_apply_df(const float4* __restrict__ Y, const double2* _
   out[e] = tot;
 }
 
+template <int NC, bool DF>
+bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s) {
+  static int cached_grid[64] = {0};
+  int& grid = cached_grid[device & 63];
+  if (grid == 0) {
+    int occ = 0, sms = 0;
+    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne<NC, DF>, kWarps * 32, 0));
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    int coop = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    if (!coop || occ < 1) return false;
+    grid = sms * (occ < 2 ? occ : 2);
+  }
+  CgneArgs a = args;
+  void* params[] = {&a};
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne<NC, DF>, dim3(grid), dim3(kWarps * 32),
+                                      params, 0, s));
+  sw_count_launch();
+  return true;
+}
+
 }  // namespace
 
 void launch_coarse_apply_df(const CoarseGeom& g, const float4* Y, int dagger, const double2* in,
@@ -449,29 +429,29 @@ void launch_coarse_apply_df(const CoarseGeom& g, const float4* Y, int dagger, co
 // host-driven loop.  partials needs 2 x grid doubles (grid <= 2 x SMs), bar 2 unsigned
 // (zeroed here), status 3 ints.
 bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const double2* b,
-                            double2* x, double2* r, double2* p, double* partials, unsigned* bar,
-                            int* status, int maxit, double tol, int device, cudaStream_t s,
-                            int stall_test) {
+                            double2* x, double2* r, double2* p, float4* rdf, float4* pdf,
+                            double* partials, unsigned* bar, int* status, int maxit, double tol,
+                            int device, cudaStream_t s, int stall_test) {
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));
-  CgneArgs a{Y, b, x, r, p, partials, bar, status, g.E0, g.E1, maxit, tol, stall_test};
-  int grid = 0;
+  CgneArgs a{Y, b, x, r, p, rdf, pdf, partials, bar, status, g.E0, g.E1, maxit, tol, stall_test};
   if (df64) {
+    if (!rdf || !pdf) return false;
     switch (g.nc) {
-      case 16: return launch_cgne_t<16, 8, true>(a, device, s, &grid);
-      case 24: return launch_cgne_t<24, 8, true>(a, device, s, &grid);
-      case 32: return launch_cgne_t<32, 16, true>(a, device, s, &grid);
-      case 48: return launch_cgne_t<48, 16, true>(a, device, s, &grid);
-      case 64: return launch_cgne_t<64, 16, true>(a, device, s, &grid);
+      case 16: return launch_cgne_t<16, true>(a, device, s);
+      case 24: return launch_cgne_t<24, true>(a, device, s);
+      case 32: return launch_cgne_t<32, true>(a, device, s);
+      case 48: return launch_cgne_t<48, true>(a, device, s);
+      case 64: return launch_cgne_t<64, true>(a, device, s);
       default: return false;
     }
   }
   switch (g.nc) {
-    case 16: return launch_cgne_t<16, 8, false>(a, device, s, &grid);
-    case 24: return launch_cgne_t<24, 8, false>(a, device, s, &grid);
-    case 32: return launch_cgne_t<32, 16, false>(a, device, s, &grid);
-    case 48: return launch_cgne_t<48, 16, false>(a, device, s, &grid);
-    case 64: return launch_cgne_t<64, 16, false>(a, device, s, &grid);
+    case 16: return launch_cgne_t<16, false>(a, device, s);
+    case 24: return launch_cgne_t<24, false>(a, device, s);
+    case 32: return launch_cgne_t<32, false>(a, device, s);
+    case 48: return launch_cgne_t<48, false>(a, device, s);
+    case 64: return launch_cgne_t<64, false>(a, device, s);
     default: return false;
   }
 }

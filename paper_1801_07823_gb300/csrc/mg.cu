@@ -256,7 +256,8 @@ static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
     bool df = mg->mixed && L.Ydf;
     bool ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, df ? (const void*)L.Ydf
                                                                       : (const void*)L.Y,
-                                      df ? 1 : 0, b, x, L.gr, L.cp,
+                                      df ? 1 : 0, b, x, L.gr, L.cp, L.cdf,
+                                      L.cdf ? L.cdf + L.ndof : nullptr,
                                       c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
                                       mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
     timing_end(c, tk);
@@ -456,6 +457,7 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
       } else {  // coarsest level: double-float copy
         C.Ydf = (float4*)mg_alloc(mg, ysz);
         launch_to_df64(C.Y, C.Ydf, ysz, s);
+        C.cdf = (float4*)mg_alloc(mg, 2 * C.ndof);
       }
     }
     SW_CUDA(cudaStreamSynchronize(s));

@@ -198,11 +198,12 @@ void launch_coarse_apply(const CoarseGeom& g, const double2* Y, int dagger, cons
                          unsigned long long* exec = nullptr);
 // Whole coarsest-level CGNE in one cooperative launch (cgne.cu); false when nc
 // has no compiled variant.
-// Y: complex128 stencil (df64 = 0) or double-float float4 stencil (df64 = 1).
+// Y: complex128 stencil (df64 = 0) or double-float float4 stencil (df64 = 1,
+// then rdf and pdf are n float4 of scratch).
 bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const double2* b,
-                            double2* x, double2* r, double2* p, double* partials, unsigned* bar,
-                            int* status, int maxit, double tol, int device, cudaStream_t s,
-                            int stall_test = 0);
+                            double2* x, double2* r, double2* p, float4* rdf, float4* pdf,
+                            double* partials, unsigned* bar, int* status, int maxit, double tol,
+                            int device, cudaStream_t s, int stall_test = 0);
 
 // ------------------------------------------------------------- mixed.cu
 void fine_apply_S32(const sw_gauge* g, const float2* W32, const float2* binv32,

@@ -17,6 +17,7 @@ struct MgLevel {
   __half2* Yh = nullptr;  // mixed precision, intermediate levels: FP16 stencil ...
   float* Ysc = nullptr;   // ... with one scale per block
   float4* Ydf = nullptr;  // mixed precision, coarsest level: double-float stencil
+  float4* cdf = nullptr;  // [2][ndof] double-float copies of r and p for its CGNE
   // setup work vectors
   double2 *sr = nullptr, *sp = nullptr, *sq = nullptr, *st = nullptr;
   // solve work vectors

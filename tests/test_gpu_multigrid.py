@@ -155,10 +155,13 @@ SOLVE_CASES = {
     # vectors from 4 passes of the setup relaxation (the small plain case).
     2: dict(L=32, beta=3.0, sweeps=1000, m=0.01, blocks=[(4, 4)], nvec=[8], passes=4),
     3: dict(L=64, beta=6.0, sweeps=300, m=0.01, blocks=[(4, 4), (2, 2)], nvec=[8, 12], passes=1),
+    # a fourth level (Sec. IV: the recursion generalises to coarser levels)
+    4: dict(L=64, beta=6.0, sweeps=300, m=0.01, blocks=[(2, 2), (2, 2), (2, 2)], nvec=[4, 6, 8],
+            passes=1),
 }
 
 
-@pytest.mark.parametrize("levels", [2, 3])
+@pytest.mark.parametrize("levels", [2, 3, 4])
 def test_solve_parity(sw, ctx, levels):
     """MG solve: true residual <= 1e-10 recomputed by the oracle's D, solution
     and iteration counts within 10% of the oracle's (outer iterations and fine
