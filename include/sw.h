@@ -40,13 +40,23 @@ enum {
   SW_ERR_TIMEOUT = -8    /* a bounded device-side wait gave up */
 };
 
-enum { SW_OP_D = 0, SW_OP_DDAG = 1, SW_OP_A = 2, SW_OP_ADAG = 3, SW_OP_S = 4 };
+enum {
+  SW_OP_D = 0,
+  SW_OP_DDAG = 1,
+  SW_OP_A = 2,
+  SW_OP_ADAG = 3,
+  SW_OP_S = 4,
+  SW_OP_DNAIK = 5,
+  SW_OP_ANAIK = 6
+};
 /* Arithmetic of an operator application: FP64; FP32; FP16S = FP16 storage with
  * one FP32 scale per stencil block and FP32 accumulation; DF64 = double-float
  * (pairs of FP32 numbers, 48-bit significand) on the FP32 pipes. */
 enum { SW_PREC_FP64 = 0, SW_PREC_FP32 = 1, SW_PREC_FP16S = 2, SW_PREC_DF64 = 3 };
 /* Precision of a multigrid hierarchy (sw_mg_params.precision). */
 enum { SW_MG_FP64 = 0, SW_MG_MIXED = 1 };
+/* Operator a hierarchy coarsens (sw_mg_params.fine_operator). */
+enum { SW_MG_COARSEN_A = 0, SW_MG_COARSEN_D = 1 };
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_gauge sw_gauge;
@@ -74,6 +84,12 @@ typedef struct {
                             K-cycle the fine S runs in FP32, intermediate-level
                             stencils in FP16S, and the coarsest CGNE applies its
                             stencil in DF64. */
+  int fine_operator;     /* SW_MG_COARSEN_A (default): the paper's method, Galerkin
+                            coarsening of A = D B^-1 with the Schur outer solve.
+                            SW_MG_COARSEN_D: the same recipe applied to D itself
+                            (P^dag D P, outer FGCR and MR on the full D), the
+                            variant Sec. III.B shows to stall; FP64 only.  Level-1
+                            transfers then act on all sites. */
 } sw_mg_params;
 
 /* Per-solve counters.  "fine applies" counts applications of the level-1
@@ -117,8 +133,15 @@ void sw_gauge_free(sw_gauge* g);
  *  SW_OP_ADAG its adjoint.
  *  SW_OP_S    Schur operator I - A_eo A_oe on the even KD blocks (Table kcycle):
  *             odd-block entries of in are ignored, of out are written as 0.
+ *  SW_OP_DNAIK Naik-improved operator (Sec. II.A, Eq. freehisq) in Eq.
+ *             staggeredD's sign and 1/2 normalisation: one-link hops x 9/8,
+ *             three-link hops x (-1/24) carrying U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+ *             (the paper prints the free operator only).
+ *  SW_OP_ANAIK D_Naik B_Naik^-1 with B_Naik its 2x2-block part (the three-link
+ *             hops always leave the block, so B_Naik = B with hops x 9/8).
  * precision: SW_PREC_FP64 (complex128 buffers) or SW_PREC_FP32 (complex64
- * buffers; SW_OP_D and SW_OP_DDAG only).  mass must be > 0 for A, ADAG, S. */
+ * buffers; SW_OP_D and SW_OP_DDAG only).  mass must be > 0 for A, ADAG, S,
+ * ANAIK.  The Naik ops build the long links (and B_Naik^-1) on first use. */
 int sw_dslash(sw_gauge* g, double mass, int op, int precision, const void* in, void* out,
               int on_device);
 
@@ -192,7 +215,8 @@ int sw_mg_export_Y(sw_mg* mg, int level, double* Y);
  * sw_mg_apply_level: out = op_l(in).  Level 1: the Schur operator
  *   I - A_eo A_oe on [L1][L0] complex128 fields (odd-block entries of in
  *   ignored, of out written 0), precision SW_PREC_FP64, or SW_PREC_FP32 on a
- *   mixed hierarchy; dagger must be 0.  Level >= 2: the coarse stencil A_hat
+ *   mixed hierarchy; on a SW_MG_COARSEN_D hierarchy, D on all sites; dagger
+ *   must be 0.  Level >= 2: the coarse stencil A_hat
  *   (dagger = 1: A_hat^dag) on [sites][nc] complex128 (Sec. III: A_hat =
  *   P^dag A P as the nearest-neighbour stencil of the export above) in
  *   SW_PREC_FP64, or in the reduced copy a mixed hierarchy keeps for that

@@ -133,13 +133,20 @@ class Hierarchy:
     computed on level l+1.  psi0[l] = list of initial vectors on level l+1 (from
     sw_inputs), each of length ndof(l+1)."""
 
-    def __init__(self, theta, m, levels, blocks, nvec, psi0, params: Params = None):
+    def __init__(self, theta, m, levels, blocks, nvec, psi0, params: Params = None,
+                 fine_op: str = "A"):
+        """fine_op = "A": the paper's method (coarsen A = D B^-1, Schur outer
+        solve).  fine_op = "D": the Galerkin MG of D itself (Sec. III.B, the
+        variant the paper shows to stall), same recipe with D in place of A and
+        the outer solve on the full D."""
         self.p = params or Params()
         self.F = FineOperators(theta, m)
+        self.fine_op = fine_op
         F = self.F
         self.levels = []
         ext = (F.L0, F.L1)
-        lev = Level(op=F.A, opdag=F.Adag, chir=F.eps, extent=ext, nc=1)
+        fop = F.A if fine_op == "A" else F.D
+        lev = Level(op=fop, opdag=fop.conj().T.tocsr(), chir=F.eps, extent=ext, nc=1)
         self.levels.append(lev)
         for l in range(levels - 1):
             nv = nvec[l]
@@ -212,6 +219,24 @@ class Hierarchy:
             return x1 + e + x3
 
         bn = norm(b)
+        if self.fine_op == "D":
+            def Dop(v):
+                st["fine_applies"] += 1
+                return F.D @ v
+
+            def kcycle_D(r):
+                x1, r1 = krylov.mr(Dop, r, p.smoother_iters, p.omega)
+                ehat = solve_level(1, self.levels[0].P.conj().T @ r1)
+                e = self.levels[0].P @ ehat
+                r2 = r1 - Dop(e)
+                x3, _ = krylov.mr(Dop, r2, p.smoother_iters, p.omega)
+                return x1 + e + x3
+            x, it, rs, conv = krylov.fgcr(Dop, kcycle_D, b.astype(complex), tol * bn,
+                                          p.outer_restart, p.outer_maxiter, confirm=True,
+                                          on_iter=on_outer)
+            st.update(outer_iters=it, restarts=rs, converged=conv,
+                      true_resid=norm(b - F.D @ x) / bn)
+            return x, st
         bt = F.schur_rhs(b)
         precond = kcycle_fine if nlev > 1 else (lambda r: r)
         ze, it, rs, conv = krylov.fgcr(S, precond, bt, tol * bn, p.outer_restart, p.outer_maxiter,

@@ -43,6 +43,48 @@ def dirac(theta: np.ndarray, m: float) -> sp.csr_matrix:
                          shape=(N, N)).tocsr()
 
 
+NAIK_C1, NAIK_C3 = 9.0 / 8.0, -1.0 / 24.0
+
+
+def dirac_naik(theta: np.ndarray, m: float) -> sp.csr_matrix:
+    """Naik-improved staggered operator (Sec. II.A, Eq. freehisq), in the sign and
+    1/2 normalisation of Eq. staggeredD: one-link hops weighted c1 = 9/8 and
+    three-link hops weighted c3 = -1/24 (so 1/2 c1 = 9/16, 1/2 c3 = -1/48 as
+    printed; free symbol sin p (1 + sin^2 p / 6)).  The paper gives the free
+    operator only; the three-link hop here carries the product of the three
+    links along its path, U_mu(x) U_mu(x+mu) U_mu(x+2mu)."""
+    _, L1, L0 = theta.shape
+    N = L0 * L1
+    U = links(theta)
+    et = lattice.eta(L0, L1)
+    x0, x1 = lattice.coords(L0, L1)
+    s = np.arange(N)
+    rows, cols, vals = [s], [s], [np.full(N, m, dtype=complex)]
+    for mu in range(2):
+        d0, d1 = (1, 0) if mu == 0 else (0, 1)
+        nb = [lattice.site(x0 + k * d0, x1 + k * d1, L0, L1) for k in range(-3, 4)]
+        f1, b1, f3, b3 = nb[4], nb[2], nb[6], nb[0]
+        long_f = U[mu] * U[mu][f1] * U[mu][nb[5]]          # U(x) U(x+mu) U(x+2mu)
+        long_b = U[mu][b3] * U[mu][nb[1]] * U[mu][b1]      # U(x-3mu) U(x-2mu) U(x-mu)
+        rows += [s, s, s, s]
+        cols += [f1, b1, f3, b3]
+        vals += [0.5 * NAIK_C1 * et[mu] * U[mu], -0.5 * NAIK_C1 * et[mu] * np.conj(U[mu][b1]),
+                 0.5 * NAIK_C3 * et[mu] * long_f, -0.5 * NAIK_C3 * et[mu] * np.conj(long_b)]
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N)).tocsr()
+
+
+def naik_kd_operator(theta: np.ndarray, m: float):
+    """(D_Naik, B_Naik, A_Naik = D_Naik B_Naik^-1): the KD split of the Naik operator
+    (Sec. II.A): three-link hops always leave the 2x2 block, so B_Naik is B with
+    its hops scaled by c1 = 9/8."""
+    _, L1, L0 = theta.shape
+    Dn = dirac_naik(theta, m)
+    Bn, _ = block_split(Dn, L0, L1)
+    An = (Dn @ block_inverse(Bn, L0, L1)).tocsr()
+    return Dn, Bn, An
+
+
 def block_split(Dm: sp.csr_matrix, L0: int, L1: int):
     """D = B + C (Sec. II.A): B keeps the entries of D that couple two sites of
     the same 2x2 Kaehler-Dirac block (the mass term included), C the rest."""

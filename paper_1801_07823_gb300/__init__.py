@@ -14,8 +14,9 @@ import os
 import numpy as np
 
 __all__ = [
-    "SwError", "lib", "SW_OP_D", "SW_OP_DDAG", "SW_OP_A", "SW_OP_ADAG", "SW_OP_S",
-    "SW_PREC_FP64", "SW_PREC_FP32", "SW_PREC_FP16S", "SW_PREC_DF64", "SW_MG_FP64", "SW_MG_MIXED",
+    "SwError", "lib", "SW_OP_D", "SW_OP_DDAG", "SW_OP_A", "SW_OP_ADAG", "SW_OP_S", "SW_OP_DNAIK",
+    "SW_OP_ANAIK",
+    "SW_PREC_FP64", "SW_PREC_FP32", "SW_PREC_FP16S", "SW_PREC_DF64", "SW_MG_FP64", "SW_MG_MIXED", "SW_MG_COARSEN_A", "SW_MG_COARSEN_D",
     "sw_context_create", "sw_context_free", "sw_last_error",
     "sw_gauge_load", "sw_gauge_free", "sw_dslash", "sw_mg_params_default", "sw_mg_setup",
     "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
@@ -24,9 +25,10 @@ __all__ = [
     "sw_dslash_schur_noalloc", "sw_debug_cgne_stall", "sw_cg_eo_solve",
 ]
 
-SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S = 0, 1, 2, 3, 4
+SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S, SW_OP_DNAIK, SW_OP_ANAIK = 0, 1, 2, 3, 4, 5, 6
 SW_PREC_FP64, SW_PREC_FP32, SW_PREC_FP16S, SW_PREC_DF64 = 0, 1, 2, 3
 SW_MG_FP64, SW_MG_MIXED = 0, 1
+SW_MG_COARSEN_A, SW_MG_COARSEN_D = 0, 1
 ERRORS = {0: "SW_OK", -1: "SW_ERR_ARG", -2: "SW_ERR_SHAPE", -3: "SW_ERR_OOM", -4: "SW_ERR_NOCONV",
           -5: "SW_ERR_BREAKDOWN", -6: "SW_ERR_NAN", -7: "SW_ERR_CUDA", -8: "SW_ERR_TIMEOUT"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsw.so")
@@ -45,7 +47,7 @@ class sw_mg_params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("inter_restart", ctypes.c_int),
                 ("inter_maxiter", ctypes.c_int), ("inter_tol", ctypes.c_double),
                 ("coarsest_maxiter", ctypes.c_int), ("coarsest_tol", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("fine_operator", ctypes.c_int)]
 
 
 class sw_solve_stats(ctypes.Structure):

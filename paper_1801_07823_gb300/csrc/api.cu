@@ -131,6 +131,7 @@ void sw_mg_params_default(sw_mg_params* p) {
   p->coarsest_maxiter = 256;
   p->coarsest_tol = 0.2;
   p->precision = SW_MG_FP64;
+  p->fine_operator = SW_MG_COARSEN_A;
 }
 
 uint64_t sw_stream_seed(uint64_t seed, int level, int index) {
@@ -256,6 +257,8 @@ void sw_gauge_free(sw_gauge* g) {
   cudaFree(g->W_ps);
   cudaFree(g->W_ps32);
   cudaFree(g->binv);
+  cudaFree(g->W3_lex);
+  cudaFree(g->binv_naik);
   for (auto& t : g->tmp) cudaFree(t);
   delete g;
 }
@@ -265,13 +268,14 @@ int sw_dslash(sw_gauge* g, double mass, int op, int precision, const void* in, v
   if (!g || !in || !out) return SW_ERR_ARG;
   sw_ctx* c = g->ctx;
   return guarded(c, [&] {
-    SW_REQUIRE(op >= SW_OP_D && op <= SW_OP_S, SW_ERR_ARG, "unknown op");
+    SW_REQUIRE(op >= SW_OP_D && op <= SW_OP_ANAIK, SW_ERR_ARG, "unknown op");
     SW_REQUIRE(precision == SW_PREC_FP64 || precision == SW_PREC_FP32, SW_ERR_ARG,
                "unknown precision");
     SW_REQUIRE(precision == SW_PREC_FP64 || op <= SW_OP_DDAG, SW_ERR_ARG,
                "FP32 is available for D and D^dag only");
     SW_REQUIRE(std::isfinite(mass), SW_ERR_ARG, "mass must be finite");
-    SW_REQUIRE(op <= SW_OP_DDAG || mass > 0.0, SW_ERR_ARG, "A, A^dag and S need mass > 0");
+    SW_REQUIRE(op <= SW_OP_DDAG || op == SW_OP_DNAIK || mass > 0.0, SW_ERR_ARG,
+               "A, A^dag, S and the Naik A need mass > 0");
     cudaStream_t s = c->stream;
     size_t N = g->N;
     size_t esz = precision == SW_PREC_FP64 ? sizeof(double2) : sizeof(float2);
@@ -284,7 +288,32 @@ int sw_dslash(sw_gauge* g, double mass, int op, int precision, const void* in, v
       din = g->tmp[0];
       dout = g->tmp[1];
     }
-    if (op <= SW_OP_DDAG) {
+    if (op == SW_OP_DNAIK || op == SW_OP_ANAIK) {
+      const double c1 = 9.0 / 8.0, c3 = -1.0 / 24.0;
+      if (!g->W3_lex) {
+        g->W3_lex = dmalloc<double2>(2 * N);
+        launch_long_links(g, c3, g->W3_lex, s);
+      }
+      if (op == SW_OP_DNAIK) {
+        launch_dslash_naik_lex(g, g->W3_lex, mass, c1, (const double2*)din, (double2*)dout, s);
+      } else {
+        for (int t = 2; t < 4; ++t)
+          if (!g->tmp[t]) g->tmp[t] = dmalloc<double2>(N);
+        if (!g->binv_naik) g->binv_naik = dmalloc<double2>(N * 4);
+        if (g->naik_mass != mass) {
+          launch_binv_build(g, mass, g->binv_naik, s, c1);
+          g->naik_mass = mass;
+        }
+        // A_Naik = D_Naik B_Naik^-1: t = B^-1 x per KD block, y = D_Naik t
+        double2* a = g->tmp[2];
+        double2* b = g->tmp[3];
+        launch_pack(g, (const double2*)din, a, s);
+        launch_block_apply(g, g->binv_naik, 0, 0, a, b, s);
+        launch_block_apply(g, g->binv_naik, 1, 0, a + N / 2, b + N / 2, s);
+        launch_unpack(g, b, a, s);
+        launch_dslash_naik_lex(g, g->W3_lex, mass, c1, a, (double2*)dout, s);
+      }
+    } else if (op <= SW_OP_DDAG) {
       if (precision == SW_PREC_FP64)
         launch_dslash_lex(g, mass, op == SW_OP_DDAG, (const double2*)din, (double2*)dout, s);
       else
@@ -343,6 +372,11 @@ int sw_mg_setup(sw_gauge* g, double mass, int levels, const int* block, const in
     SW_REQUIRE(p.precision == SW_MG_FP64 || p.precision == SW_MG_MIXED, SW_ERR_ARG,
                "unknown precision");
     mg->mixed = p.precision == SW_MG_MIXED;
+    SW_REQUIRE(p.fine_operator == SW_MG_COARSEN_A || p.fine_operator == SW_MG_COARSEN_D,
+               SW_ERR_ARG, "unknown fine_operator");
+    mg->fine_D = p.fine_operator == SW_MG_COARSEN_D;
+    SW_REQUIRE(!(mg->fine_D && mg->mixed), SW_ERR_ARG,
+               "the Galerkin MG of D is provided in FP64 only");
     SW_REQUIRE(p.setup_maxiter >= 0 && p.setup_passes >= 1 && p.outer_restart >= 1 &&
                    p.outer_maxiter >= 0 && p.smoother_iters >= 0 && p.inter_restart >= 1 &&
                    p.inter_maxiter >= 0 && p.coarsest_maxiter >= 0,
@@ -526,7 +560,9 @@ int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const voi
                  "level 1: FP64, or FP32 on a mixed-precision hierarchy");
       launch_pack(g, a, t, s);
       SW_CUDA(cudaMemsetAsync(a, 0, n * sizeof(double2), s));
-      if (precision == SW_PREC_FP64)
+      if (mg->fine_D)
+        launch_dslash_ps(g, mg->mass, 0, t, a, s);
+      else if (precision == SW_PREC_FP64)
         fine_apply_S(g, mg->binv, t, a, b, s);
       else
         fine_apply_S32(g, g->W_ps32, mg->binv32, t, a, mg->s32tmp, s);
@@ -574,10 +610,10 @@ int sw_mg_transfer(sw_mg* mg, int level, int dir, const void* in, void* out, int
     if (level == 1) {
       if (dir == 0) {
         launch_pack(g, a, t, s);
-        launch_restrict_fine(g, L.b0, L.b1, L.nv, L.P, t, b, s);
+        launch_restrict_fine(g, L.b0, L.b1, L.nv, L.P, t, b, s, mg->fine_D ? 1 : 0);
       } else {
         SW_CUDA(cudaMemsetAsync(t, 0, nf * sizeof(double2), s));
-        launch_prolong_fine(g, L.b0, L.b1, L.nv, L.P, a, t, s);
+        launch_prolong_fine(g, L.b0, L.b1, L.nv, L.P, a, t, s, mg->fine_D ? 1 : 0);
         launch_unpack(g, t, b, s);
       }
     } else {

@@ -142,8 +142,11 @@ __global__ void __launch_bounds__(5 * NC) k_coarse_apply_nc(const double2* __res
 // Level-1 transfer, even parity half only (Sec. IV: coarsen with the odd
 // contributions set to zero, keep the even part of the prolonged error).
 // Chirality eps of site k of a KD block: + for k = 0, 3 and - for k = 1, 2.
+// full = 1: r is a full parity-split vector and every KD block of the
+// aggregate contributes (used when the fine operator is D itself).
 __global__ void k_restrict_fine(const double2* __restrict__ P, const double2* __restrict__ r_e,
-                                double2* __restrict__ out, int L0, int a0, int a1, int nv) {
+                                double2* __restrict__ out, int L0, int L1, int a0, int a1, int nv,
+                                int full) {
   int A = blockIdx.x;
   int E0 = L0 / (2 * a0);
   int A0 = A % E0, A1 = A / E0;
@@ -152,11 +155,13 @@ __global__ void k_restrict_fine(const double2* __restrict__ P, const double2* __
   int c = t / nv, i = t - c * nv;
   int ka = c ? 1 : 0, kb = c ? 2 : 3;
   double2 acc = make_double2(0.0, 0.0);
+  int half = (L0 * L1) >> 1;
   for (int by = 0; by < a1; ++by)
     for (int bx = 0; bx < a0; ++bx) {
       int X0 = A0 * a0 + bx, X1 = A1 * a1 + by;
-      if ((X0 + X1) & 1) continue;
-      int hb = X1 * (L0 >> 2) + (X0 >> 1);
+      int par = (X0 + X1) & 1;
+      if (par && !full) continue;
+      int hb = par * half + X1 * (L0 >> 2) + (X0 >> 1);
       int ha = 4 * hb + ka, hc = 4 * hb + kb;
       cfmac(acc, P[(long)ha * nv + i], r_e[ha]);
       cfmac(acc, P[(long)hc * nv + i], r_e[hc]);
@@ -165,10 +170,11 @@ __global__ void k_restrict_fine(const double2* __restrict__ P, const double2* __
 }
 
 __global__ void k_prolong_fine(const double2* __restrict__ P, const double2* __restrict__ ehat,
-                               double2* __restrict__ e_e, int L0, int L1, int a0, int a1, int nv) {
+                               double2* __restrict__ e_e, int L0, int L1, int a0, int a1, int nv,
+                               int full) {
   int N = L0 * L1;
   int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= N / 2) return;
+  if (h >= (full ? N : N / 2)) return;
   int x0, x1;
   ps_coords(h, L0, N, x0, x1);
   int E0 = L0 / (2 * a0);
@@ -239,6 +245,20 @@ __global__ void k_build_W(const double2* __restrict__ binv, const double2* __res
   cfma(w1, m[2], P[(long)(4 * b + 2) * nv + i]);
   Wv[((long)f * 2 + 0) * nv + i] = w0;
   Wv[((long)f * 2 + 1) * nv + i] = w1;
+}
+
+// Wv from P alone (no B^-1): Wv[f][c][i] = P[f][i] if chirality(f) = c, else 0
+// -- the Galerkin build of D itself.
+__global__ void k_build_W_identity(const double2* __restrict__ P, double2* __restrict__ Wv, int N,
+                                   int nv) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)N * nv) return;
+  int f = (int)(e / nv), i = (int)(e - (long)f * nv);
+  int k = f & 3;
+  int c = (k == 1 || k == 2);
+  double2 z = make_double2(0.0, 0.0), v = P[e];
+  Wv[((long)f * 2 + 0) * nv + i] = c == 0 ? v : z;
+  Wv[((long)f * 2 + 1) * nv + i] = c == 1 ? v : z;
 }
 
 struct HopTerm {
@@ -551,15 +571,16 @@ void launch_coarse_apply(const CoarseGeom& g, const double2* Y, int dagger, cons
   SW_LAUNCH_CHECK();
 }
 void launch_restrict_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,
-                          const double2* r_e, double2* out, cudaStream_t s) {
+                          const double2* r_e, double2* out, cudaStream_t s, int full) {
   int nagg = (g->L0 / (2 * a0)) * (g->L1 / (2 * a1));
   int threads = cdiv(2 * nv, 32) * 32;
-  k_restrict_fine<<<nagg, threads, 0, s>>>(P, r_e, out, g->L0, a0, a1, nv);
+  k_restrict_fine<<<nagg, threads, 0, s>>>(P, r_e, out, g->L0, g->L1, a0, a1, nv, full);
   SW_LAUNCH_CHECK();
 }
 void launch_prolong_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,
-                         const double2* ehat, double2* e_e, cudaStream_t s) {
-  k_prolong_fine<<<cdiv(g->N / 2, 128), 128, 0, s>>>(P, ehat, e_e, g->L0, g->L1, a0, a1, nv);
+                         const double2* ehat, double2* e_e, cudaStream_t s, int full) {
+  k_prolong_fine<<<cdiv(full ? g->N : g->N / 2, 128), 128, 0, s>>>(P, ehat, e_e, g->L0, g->L1, a0,
+                                                                   a1, nv, full);
   SW_LAUNCH_CHECK();
 }
 void launch_restrict_coarse(const CoarseGeom& g, int b0, int b1, int nv, const double2* P,
@@ -579,6 +600,12 @@ void launch_build_W(const sw_gauge* g, int nv, const double2* binv, const double
                     double2* Wv, cudaStream_t s) {
   long n = (long)g->N * nv;
   k_build_W<<<cdiv(n, 256), 256, 0, s>>>(binv, P, Wv, g->N, nv);
+  SW_LAUNCH_CHECK();
+}
+void launch_build_W_identity(const sw_gauge* g, int nv, const double2* P, double2* Wv,
+                             cudaStream_t s) {
+  long n = (long)g->N * nv;
+  k_build_W_identity<<<cdiv(n, 256), 256, 0, s>>>(P, Wv, g->N, nv);
   SW_LAUNCH_CHECK();
 }
 void launch_build_Y_fine(const sw_gauge* g, double mass, int a0, int a1, int nv, const double2* P,

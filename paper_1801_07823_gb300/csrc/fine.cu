@@ -89,8 +89,8 @@ __global__ void k_unpack(const double2* __restrict__ ps, double2* __restrict__ l
 // block of site k is k ^ (1 << mu): a forward hop (coefficient W_mu(s)) when
 // x_mu is even, a backward hop (coefficient -conj(W_mu(s - mu))) when odd.
 // Inverted by Gauss-Jordan elimination with partial pivoting in FP64.
-__global__ void k_binv_build(const double2* __restrict__ Wps, double mass, double2* __restrict__ binv,
-                             int L0, int L1) {
+__global__ void k_binv_build(const double2* __restrict__ Wps, double mass, double hop_scale,
+                             double2* __restrict__ binv, int L0, int L1) {
   int N = L0 * L1;
   int nb = N >> 2;
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,10 +109,11 @@ __global__ void k_binv_build(const double2* __restrict__ Wps, double mass, doubl
       int kp = k ^ (1 << mu);
       int xm = mu == 0 ? x0 : x1;
       if ((xm & 1) == 0) {
-        M[k][kp] = Wps[mu * N + 4 * b + k];
+        double2 w = Wps[mu * N + 4 * b + k];
+        M[k][kp] = make_double2(hop_scale * w.x, hop_scale * w.y);
       } else {
         double2 w = Wps[mu * N + 4 * b + kp];  // W_mu(s - mu), s - mu is site kp
-        M[k][kp] = make_double2(-w.x, w.y);
+        M[k][kp] = make_double2(-hop_scale * w.x, hop_scale * w.y);
       }
     }
   }
@@ -234,9 +235,106 @@ __global__ void k_hop_block(const double2* __restrict__ Wps, const double2* __re
   }
 }
 
+// Long links of the Naik term (Sec. II.A, Eq. freehisq, gauged with the
+// product of the three links of the path): W3_mu(s) = c3 eta_mu(s) / 2 *
+// U_mu(s) U_mu(s+mu) U_mu(s+2mu), from W_mu = eta_mu U_mu / 2 (lexicographic).
+__global__ void k_long_links(const double2* __restrict__ W, double c3, double2* __restrict__ W3,
+                             int L0, int L1) {
+  long N = (long)L0 * L1;
+  long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int x0 = (int)(s % L0), x1 = (int)(s / L0);
+  for (int mu = 0; mu < 2; ++mu) {
+    long s1 = mu == 0 ? (long)x1 * L0 + (x0 + 1) % L0 : (long)((x1 + 1) % L1) * L0 + x0;
+    long s2 = mu == 0 ? (long)x1 * L0 + (x0 + 2) % L0 : (long)((x1 + 2) % L1) * L0 + x0;
+    double2 a = W[mu * N + s], b = W[mu * N + s1], c = W[mu * N + s2];
+    // each W carries eta / 2 with the same eta along the path (eta_1 depends
+    // on x0 only): U U U = 8 a b c / eta^3 = 8 a b c eta, so
+    // W3 = c3 (eta / 2) U U U = 4 c3 a b c
+    double2 abc = cmul(cmul(a, b), c);
+    W3[mu * N + s] = make_double2(4.0 * c3 * abc.x, 4.0 * c3 * abc.y);
+  }
+}
+
+// Naik-improved D: out(s) = m in(s) + sum_mu [c1 (W in(s+mu) - W(s-mu)^* in(s-mu))
+//                                            + W3 in(s+3mu) - W3(s-3mu)^* in(s-3mu)]
+__global__ void k_dslash_naik_lex(const double2* __restrict__ in, double2* __restrict__ out,
+                                  const double2* __restrict__ W, const double2* __restrict__ W3,
+                                  double mass, double c1, int L0, int L1) {
+  int x0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int x1 = blockIdx.y;
+  if (x0 >= L0) return;
+  long N = (long)L0 * L1;
+  long s = (long)x1 * L0 + x0;
+  double2 h1 = make_double2(0.0, 0.0), h3 = make_double2(0.0, 0.0);
+  for (int mu = 0; mu < 2; ++mu) {
+    auto site = [&](int k) {
+      return mu == 0 ? (long)x1 * L0 + ((x0 + k) % L0 + L0) % L0
+                     : (long)(((x1 + k) % L1 + L1) % L1) * L0 + x0;
+    };
+    long f1 = site(1), b1 = site(-1), f3 = site(3), b3 = site(-3);
+    cfma(h1, W[mu * N + s], in[f1]);
+    double2 w = W[mu * N + b1], v = in[b1];
+    h1.x -= w.x * v.x + w.y * v.y;
+    h1.y -= w.x * v.y - w.y * v.x;
+    cfma(h3, W3[mu * N + s], in[f3]);
+    w = W3[mu * N + b3];
+    v = in[b3];
+    h3.x -= w.x * v.x + w.y * v.y;
+    h3.y -= w.x * v.y - w.y * v.x;
+  }
+  double2 xs = in[s];
+  out[s] = make_double2(mass * xs.x + c1 * h1.x + h3.x, mass * xs.y + c1 * h1.y + h3.y);
+}
+
+// D (sg = +1) or D^dag (sg = -1) on a full parity-split vector:
+// out(f) = m in(f) + sg sum_mu [W_mu(s) in(s+mu) - conj(W_mu(s-mu)) in(s-mu)].
+__global__ void k_dslash_ps(const double2* __restrict__ Wps, double mass, double sg,
+                            const double2* __restrict__ in, double2* __restrict__ out, int L0,
+                            int L1) {
+  int N = L0 * L1;
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= N) return;
+  int x0, x1;
+  ps_coords(f, L0, N, x0, x1);
+  int xp0 = x0 + 1 == L0 ? 0 : x0 + 1, xm0 = x0 == 0 ? L0 - 1 : x0 - 1;
+  int xp1 = x1 + 1 == L1 ? 0 : x1 + 1, xm1 = x1 == 0 ? L1 - 1 : x1 - 1;
+  int fp0 = ps_index(xp0, x1, L0, N), fm0 = ps_index(xm0, x1, L0, N);
+  int fp1 = ps_index(x0, xp1, L0, N), fm1 = ps_index(x0, xm1, L0, N);
+  double2 h = make_double2(0.0, 0.0);
+  cfma(h, Wps[f], in[fp0]);
+  cfma(h, Wps[N + f], in[fp1]);
+  double2 w = Wps[fm0], v = in[fm0];
+  h.x -= w.x * v.x + w.y * v.y;
+  h.y -= w.x * v.y - w.y * v.x;
+  w = Wps[N + fm1];
+  v = in[fm1];
+  h.x -= w.x * v.x + w.y * v.y;
+  h.y -= w.x * v.y - w.y * v.x;
+  double2 xs = in[f];
+  out[f] = make_double2(fma(sg, h.x, mass * xs.x), fma(sg, h.y, mass * xs.y));
+}
+
 inline int nblocks(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+void launch_long_links(const sw_gauge* g, double c3, double2* W3, cudaStream_t s) {
+  k_long_links<<<nblocks(g->N, 256), 256, 0, s>>>(g->W_lex, c3, W3, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_dslash_naik_lex(const sw_gauge* g, const double2* W3, double mass, double c1,
+                            const double2* in, double2* out, cudaStream_t s) {
+  dim3 grid(nblocks(g->L0, 256), g->L1);
+  k_dslash_naik_lex<<<grid, 256, 0, s>>>(in, out, g->W_lex, W3, mass, c1, g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
+void launch_dslash_ps(const sw_gauge* g, double mass, int dagger, const double2* in, double2* out,
+                      cudaStream_t s) {
+  k_dslash_ps<<<nblocks(g->N, 256), 256, 0, s>>>(g->W_ps, mass, dagger ? -1.0 : 1.0, in, out,
+                                                 g->L0, g->L1);
+  SW_LAUNCH_CHECK();
+}
 
 void launch_dslash_lex(const sw_gauge* g, double mass, int dagger, const double2* in, double2* out,
                        cudaStream_t s) {
@@ -260,8 +358,10 @@ void launch_unpack(const sw_gauge* g, const double2* ps, double2* lex, cudaStrea
   k_unpack<<<nblocks(g->N, 256), 256, 0, s>>>(ps, lex, g->L0, g->L1);
   SW_LAUNCH_CHECK();
 }
-void launch_binv_build(const sw_gauge* g, double mass, double2* binv, cudaStream_t s) {
-  k_binv_build<<<nblocks(g->N / 4, 128), 128, 0, s>>>(g->W_ps, mass, binv, g->L0, g->L1);
+void launch_binv_build(const sw_gauge* g, double mass, double2* binv, cudaStream_t s,
+                       double hop_scale) {
+  k_binv_build<<<nblocks(g->N / 4, 128), 128, 0, s>>>(g->W_ps, mass, hop_scale, binv, g->L0,
+                                                      g->L1);
   SW_LAUNCH_CHECK();
 }
 void launch_block_apply(const sw_gauge* g, const double2* binv, int par, int dagger,

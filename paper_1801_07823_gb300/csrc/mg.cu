@@ -69,7 +69,8 @@ struct TempBuffers {
 // ---------------------------------------------------------------- operators
 long level_len(const sw_mg* mg, int l) {
   const MgLevel& L = mg->lev[l];
-  return l == 0 ? mg->g->N / 2 : L.ndof;
+  if (l == 0) return mg->fine_D ? mg->g->N : mg->g->N / 2;
+  return L.ndof;
 }
 
 // Operator of level l in the solve: S on level 0 (even half), A_hat below.
@@ -81,7 +82,9 @@ void level_op(sw_mg* mg, int l, const double2* in, double2* out, const int* skip
   sw_ctx* c = mg->ctx;
   int tk = timing_begin(c, l);
   if (l == 0) {
-    if (lowp && mg->mixed)
+    if (mg->fine_D)
+      launch_dslash_ps(mg->g, mg->mass, 0, in, out, c->stream);
+    else if (lowp && mg->mixed)
       fine_apply_S32(mg->g, mg->g->W_ps32, mg->binv32, in, out, mg->s32tmp, c->stream);
     else
       fine_apply_S(mg->g, mg->binv, in, out, mg->lev[0].stmp, c->stream);
@@ -108,7 +111,10 @@ void level_opdag(sw_mg* mg, int l, const double2* in, double2* out, const int* s
 // level 0).
 void level_normal(sw_mg* mg, int l, const double2* in, double2* out, double2* tmp) {
   cudaStream_t s = mg->ctx->stream;
-  if (l == 0) {
+  if (l == 0 && mg->fine_D) {
+    launch_dslash_ps(mg->g, mg->mass, 1, in, tmp, s);
+    launch_dslash_ps(mg->g, mg->mass, 0, tmp, out, s);
+  } else if (l == 0) {
     fine_apply_Adag(mg->g, mg->binv, in, tmp, s);
     fine_apply_A(mg->g, mg->binv, tmp, out, mg->lev[0].stmp, s);
   } else {
@@ -151,12 +157,12 @@ static void kcycle(sw_mg* mg, int l, const double2* r, double2* out) {
   cudaStream_t s = c->stream;
   mr(mg, l, r, L.kx1, L.kr1, L.kq);
   if (l == 0)
-    launch_restrict_fine(mg->g, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s);
+    launch_restrict_fine(mg->g, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s, mg->fine_D ? 1 : 0);
   else
     launch_restrict_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s);
   solve_level(mg, l + 1, C.rhs, C.sol);
   if (l == 0)
-    launch_prolong_fine(mg->g, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s);
+    launch_prolong_fine(mg->g, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s, mg->fine_D ? 1 : 0);
   else
     launch_prolong_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s);
   level_op(mg, l, L.ke, L.kq, nullptr, true);
@@ -442,7 +448,10 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
     C.Y = mg_alloc(mg, ysz);
     if (l == 0) {
       double2* Wv = tmp.get(N * 2 * nv);
-      launch_build_W(g, nv, mg->binv, L.P, Wv, s);
+      if (mg->fine_D)
+        launch_build_W_identity(g, nv, L.P, Wv, s);  // Galerkin of D itself: P^dag D P
+      else
+        launch_build_W(g, nv, mg->binv, L.P, Wv, s);
       launch_build_Y_fine(g, mg->mass, L.b0, L.b1, nv, L.P, Wv, C.Y, s);
     } else {
       double2* T = tmp.get((long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
@@ -518,16 +527,23 @@ int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
     }
     return SW_OK;
   }
-  // b~_e = b_e - A_eo b_o = b_e - C_eo B_o^-1 b_o
-  launch_block_apply(g, mg->binv, 1, 0, mg->bps + half, L.stmp + half, s);
-  launch_hop(g, 0, -1.0, mg->bps, L.stmp + half, L.rhs, s);
-  GcrResult r = fgcr(mg, 0, L.rhs, L.sol, tol * bn, mg->p.outer_restart, mg->p.outer_maxiter, true);
-  // z_o = b_o - C_oe B_e^-1 z_e ; x = B^-1 z
-  launch_block_apply(g, mg->binv, 0, 0, L.sol, L.stmp, s);
-  launch_hop(g, 1, -1.0, mg->bps + half, L.stmp, L.stmp + half, s);
-  launch_block_apply(g, mg->binv, 0, 0, L.sol, mg->xps, s);
-  launch_block_apply(g, mg->binv, 1, 0, L.stmp + half, mg->xps + half, s);
-  launch_unpack(g, mg->xps, x_lex, s);
+  GcrResult r;
+  if (mg->fine_D) {
+    // Galerkin MG of D itself: flexible GCR on the full D, no KD preconditioning
+    r = fgcr(mg, 0, mg->bps, L.sol, tol * bn, mg->p.outer_restart, mg->p.outer_maxiter, true);
+    launch_unpack(g, L.sol, x_lex, s);
+  } else {
+    // b~_e = b_e - A_eo b_o = b_e - C_eo B_o^-1 b_o
+    launch_block_apply(g, mg->binv, 1, 0, mg->bps + half, L.stmp + half, s);
+    launch_hop(g, 0, -1.0, mg->bps, L.stmp + half, L.rhs, s);
+    r = fgcr(mg, 0, L.rhs, L.sol, tol * bn, mg->p.outer_restart, mg->p.outer_maxiter, true);
+    // z_o = b_o - C_oe B_e^-1 z_e ; x = B^-1 z
+    launch_block_apply(g, mg->binv, 0, 0, L.sol, L.stmp, s);
+    launch_hop(g, 1, -1.0, mg->bps + half, L.stmp, L.stmp + half, s);
+    launch_block_apply(g, mg->binv, 0, 0, L.sol, mg->xps, s);
+    launch_block_apply(g, mg->binv, 1, 0, L.stmp + half, mg->xps + half, s);
+    launch_unpack(g, mg->xps, x_lex, s);
+  }
   // true residual ||b - D x|| / ||b|| in FP64
   launch_dslash_lex(g, mg->mass, 0, x_lex, mg->lext, s);
   blas_sub(c, mg->lext, b_lex, mg->lext, N);

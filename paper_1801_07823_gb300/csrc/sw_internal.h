@@ -106,6 +106,9 @@ struct sw_gauge {
   float2* W_ps32 = nullptr;   // FP32 copy of W_ps (mixed-precision Schur operator)
   double binv_mass = -1.0;
   double2* binv = nullptr;    // [N/4][4][4] B^-1 per KD block for binv_mass
+  double2* W3_lex = nullptr;  // [2][N] Naik long links (built on first use)
+  double naik_mass = -1.0;
+  double2* binv_naik = nullptr;  // B_Naik^-1 for naik_mass
   double2* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // [N] scratch for sw_dslash
 };
 
@@ -138,8 +141,17 @@ void launch_dslash_lex(const sw_gauge* g, double mass, int dagger, const double2
 void launch_dslash_lex32(const sw_gauge* g, float mass, int dagger, const float2* in, float2* out,
                          cudaStream_t s);
 void launch_pack(const sw_gauge* g, const double2* lex, double2* ps, cudaStream_t s);
+// D (or D^dag) on full parity-split vectors.
+void launch_dslash_ps(const sw_gauge* g, double mass, int dagger, const double2* in, double2* out,
+                      cudaStream_t s);
 void launch_unpack(const sw_gauge* g, const double2* ps, double2* lex, cudaStream_t s);
-void launch_binv_build(const sw_gauge* g, double mass, double2* binv, cudaStream_t s);
+// hop_scale multiplies the in-block hops (1 for D, 9/8 for the Naik operator).
+void launch_binv_build(const sw_gauge* g, double mass, double2* binv, cudaStream_t s,
+                       double hop_scale = 1.0);
+// Naik-improved operator (three-link term with the product of the path's links).
+void launch_long_links(const sw_gauge* g, double c3, double2* W3, cudaStream_t s);
+void launch_dslash_naik_lex(const sw_gauge* g, const double2* W3, double mass, double c1,
+                            const double2* in, double2* out, cudaStream_t s);
 // Block-local 4x4 multiply on the KD blocks of one parity half: out = M in or M^dag in.
 void launch_block_apply(const sw_gauge* g, const double2* binv, int par, int dagger,
                         const double2* in, double2* out, cudaStream_t s);
@@ -217,10 +229,13 @@ void launch_to_df64(const double2* Y, float4* Yd, long n, cudaStream_t s);
 void launch_coarse_apply_df(const CoarseGeom& g, const float4* Y, int dagger, const double2* in,
                             double2* out, cudaStream_t s);
 // Level-1 transfer on the even parity half.  P: [N][nv] parity-split rows.
+// full = 1: full parity-split vectors (fine operator D) instead of the even half.
 void launch_restrict_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,
-                          const double2* r_e, double2* out, cudaStream_t s);
+                          const double2* r_e, double2* out, cudaStream_t s, int full = 0);
 void launch_prolong_fine(const sw_gauge* g, int a0, int a1, int nv, const double2* P,
-                         const double2* ehat, double2* e_e, cudaStream_t s);
+                         const double2* ehat, double2* e_e, cudaStream_t s, int full = 0);
+void launch_build_W_identity(const sw_gauge* g, int nv, const double2* P, double2* Wv,
+                             cudaStream_t s);
 // Level >= 2 transfer.  P: [sites][nc][nv].
 void launch_restrict_coarse(const CoarseGeom& g, int b0, int b1, int nv, const double2* P,
                             const double2* r, double2* out, cudaStream_t s);

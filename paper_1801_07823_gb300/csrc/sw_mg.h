@@ -40,6 +40,7 @@ struct sw_mg {
   int verbose = 0;  // SW_VERBOSE=1: a stderr line per outer iteration; 2: also level 2
   double2* binv = nullptr;
   bool mixed = false;            // params.precision == SW_MG_MIXED
+  bool fine_D = false;           // params.fine_operator == SW_MG_COARSEN_D
   float2* binv32 = nullptr;      // FP32 B^-1 (mixed)
   float2* s32tmp = nullptr;      // [N] FP32 scratch of the FP32 Schur operator
   std::vector<MgLevel> lev;

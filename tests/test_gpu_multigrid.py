@@ -338,3 +338,37 @@ def test_mixed_precision_solve(sw, mixed64):
         assert st["converged"] and r <= 1e-10, (key, r)
         res[key] = st
     assert res["hmx"]["outer_iters"] <= res["h64"]["outer_iters"] + 3
+
+
+def test_galerkin_mg_of_D_negative_control(sw, ctx):
+    """P^dag D P on the GPU matches the oracle's D-variant hierarchy, and its
+    solve stalls like the oracle's while the paper's method converges."""
+    L, m = 32, 0.01
+    th = si.heatbath_u1(L, L, 6.0, 100, seed=26, device="cuda")
+    blocks, nvec = [(4, 4), (2, 2)], [8, 12]
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    fixed = params(sw, setup_tol=0.0, setup_maxiter=8, fine_operator=sw.SW_MG_COARSEN_D)
+    h = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=fixed, psi0=psi0)
+    H = omg.Hierarchy(th, m, 3, blocks, nvec, [list(a) for a in psi0],
+                      omg.Params(setup_tol=0.0, setup_maxiter=8), fine_op="D")
+    e0, e1, nc = sw.sw_mg_level_info(h, 2)
+    Ag = assemble_stencil(sw.sw_mg_export_Y(h, 2), e0, e1)
+    assert relerr(Ag, H.levels[1].op.toarray()) < 1e-10
+    h.free()
+    b = si.gaussian_complex(1003, L * L)
+    res = {}
+    for op in (sw.SW_MG_COARSEN_A, sw.SW_MG_COARSEN_D):
+        h = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=params(sw, outer_maxiter=30,
+                                                               fine_operator=op), psi0=psi0)
+        x = np.zeros_like(b)
+        res[op] = sw.sw_mg_solve(h, b, x, 1e-10, allow_noconv=True)
+        h.free()
+    HD = omg.Hierarchy(th, m, 3, blocks, nvec, [list(a) for a in psi0],
+                       omg.Params(outer_maxiter=30), fine_op="D")
+    _, sd = HD.solve(b, 1e-10)
+    assert res[sw.SW_MG_COARSEN_A]["converged"]
+    assert not res[sw.SW_MG_COARSEN_D]["converged"]
+    assert res[sw.SW_MG_COARSEN_D]["true_resid"] > 0.1 and sd["true_resid"] > 0.1
+    assert abs(np.log(res[sw.SW_MG_COARSEN_D]["true_resid"] / sd["true_resid"])) < np.log(1.5)
+    g.free()

@@ -119,3 +119,19 @@ def test_cg_even_odd_parity(sw, ctx):
     assert abs(st["outer_iters"] - k) <= max(3, 0.03 * k), (st["outer_iters"], k)
     assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-7
     g.free()
+
+
+@pytest.mark.parametrize("L0,L1", [(16, 16), (12, 20), (64, 32)])
+def test_naik_operators(sw, ctx, L0, L1):
+    """Naik-improved D (Eq. freehisq, gauged with the path's links) and its KD
+    form D_Naik B_Naik^-1 against the oracle, <= 1e-13 relative."""
+    m = 0.05
+    th = np.random.default_rng(L0 * L1).uniform(-np.pi, np.pi, (2, L1, L0))
+    g = sw.sw_gauge_load(ctx, th)
+    Dn, Bn, An = operators.naik_kd_operator(th, m)
+    v = si.gaussian_complex(23, L0 * L1)
+    for op, mat in ((sw.SW_OP_DNAIK, Dn), (sw.SW_OP_ANAIK, An)):
+        out = np.zeros_like(v)
+        sw.sw_dslash(g, m, op, sw.SW_PREC_FP64, v, out)
+        assert relerr(out, mat @ v) < 1e-13, (op, relerr(out, mat @ v))
+    g.free()

@@ -149,3 +149,24 @@ def test_three_level_solve_converges():
     assert st["inter_solves"] == st["outer_iters"] and st["coarsest_solves"] == st["inter_iters"]
     # six Schur applications per outer iteration (MR 2 + 1 + MR 2 + GCR 1)
     assert st["fine_applies"] >= 6 * st["outer_iters"]
+
+
+def test_galerkin_mg_of_D_stalls():
+    """Sec. III.B, Fig. residstag: the same recipe applied to D itself (P^dag D P)
+    stalls, while coarsening the KD-preconditioned A converges (oracle)."""
+    L = 32
+    th = si.heatbath_u1(L, L, 6.0, 100, seed=26)
+    p0 = psi0_for(L, [8, 12], 3)
+    b = si.gaussian_complex(1003, L * L)
+    prm = mg.Params(outer_maxiter=30)
+    HA = mg.Hierarchy(th, 0.01, 3, [(4, 4), (2, 2)], [8, 12], p0, prm)
+    HD = mg.Hierarchy(th, 0.01, 3, [(4, 4), (2, 2)], [8, 12], p0, prm, fine_op="D")
+    _, sa = HA.solve(b, 1e-10)
+    _, sd = HD.solve(b, 1e-10)
+    assert sa["converged"] and sa["outer_iters"] < 30
+    assert not sd["converged"] and sd["true_resid"] > 0.1
+    # the D hierarchy is the literal Galerkin product of D
+    P = HD.levels[0].P.toarray()
+    Dd = HD.F.D.toarray()
+    Ah = HD.levels[1].op.toarray()
+    assert np.max(np.abs(Ah - P.conj().T @ Dd @ P)) < 1e-13

@@ -259,3 +259,59 @@ def test_cg_even_odd_solves_the_system():
     x, k = operators.cg_eo_solve(th, m, b, 1e-10, 10000)
     assert np.linalg.norm(b - D @ x) / np.linalg.norm(b) <= 1e-10
     assert np.max(np.abs(x - np.linalg.solve(D, b))) / np.max(np.abs(x)) < 1e-8
+
+
+@pytest.mark.parametrize("m", [0.0, 0.2])
+def test_naik_free_spectrum(m):
+    """Eq. freehisq: lambda = m +- i sqrt(sum_mu sin^2 p (1 + sin^2 p / 6)^2), each twice."""
+    L = 16
+    ev = np.linalg.eigvals(operators.dirac_naik(np.zeros((2, L, L)), m).toarray())
+    n = np.arange(-L // 4 + 1, L // 4 + 1)
+    p = 2 * np.pi * n / L
+    f = (np.sin(p) * (1 + np.sin(p) ** 2 / 6)) ** 2
+    s = np.sqrt(f[:, None] + f[None, :]).ravel()
+    exp = np.concatenate([m + 1j * s, m - 1j * s, m + 1j * s, m - 1j * s])
+    key = lambda z: np.lexsort((np.round(z.real, 9), np.round(z.imag, 9)))
+    assert np.max(np.abs(ev[key(ev)] - exp[key(exp)])) < 1e-12
+
+
+def test_naik_kd_free_spectrum_and_block():
+    """Sec. II.A, Naik paragraph: B_Naik is the unimproved block with its hops
+    rescaled (9/8 here, 9/16 in the printed normalisation), and the massless
+    free KD spectrum is 1 - [(1-x) S1 + x S2] +- i sqrt(1 - [(1-x) S1 + x S2]^2
+    - 2x [S2 - S1 + x (S3 - 1)]), S_n = (1/2) sum_mu cos(n p_mu), x = -1/27."""
+    L = 16
+    th = np.zeros((2, L, L))
+    Dn, Bn, An = operators.naik_kd_operator(th, 0.0)
+    B = operators.FineOperators(th, 0.3).B.toarray() - 0.3 * np.eye(L * L)
+    assert np.max(np.abs(Bn.toarray() - 9.0 / 8.0 * B)) < 1e-15
+    ev = np.linalg.eigvals(An.toarray())
+    x = (-1.0 / 48.0) / (9.0 / 16.0)
+    p = 2 * np.pi * np.arange(L // 2) / (L // 2)
+    P0, P1 = np.meshgrid(p, p, indexing="ij")
+    S = lambda k: 0.5 * (np.cos(k * P0) + np.cos(k * P1)).ravel()
+    c = (1 - x) * S(1) + x * S(2)
+    im = np.sqrt((1 - c * c - 2 * x * (S(2) - S(1) + x * (S(3) - 1))).astype(complex))
+    exp = np.concatenate([1 - c + 1j * im, 1 - c - 1j * im] * 2)
+    assert spectra_distance(ev, exp) < 1e-7  # square-root branch points cost precision
+
+
+def spectra_distance(a, b):
+    """Largest distance of the optimal one-to-one matching of two spectra."""
+    from scipy.optimize import linear_sum_assignment
+    cost = np.abs(a[:, None] - b[None, :])
+    r, c = linear_sum_assignment(cost)
+    return float(cost[r, c].max())
+
+
+def test_naik_invariants():
+    """The gauged Naik operator keeps eps-Hermiticity and gauge covariance."""
+    L, m = 12, 0.1
+    th = rand_theta(L, 40)
+    Dn = operators.dirac_naik(th, m).toarray()
+    eps = np.diag(lattice.epsilon(L, L).astype(float))
+    assert np.max(np.abs(eps @ Dn @ eps - Dn.conj().T)) < 1e-15
+    alpha = np.random.default_rng(41).uniform(-np.pi, np.pi, (L, L))
+    G = np.diag(np.exp(1j * alpha.ravel()))
+    Dg = operators.dirac_naik(si.gauge_transform(th, alpha), m).toarray()
+    assert np.max(np.abs(Dg - G @ Dn @ G.conj().T)) < 1e-14
