@@ -175,7 +175,15 @@ int sw_mg_solve(sw_mg* mg, const void* b, void* x, double tol, int on_device,
                 sw_solve_stats* st);
 
 /* nrhs independent solves: B and X are [nrhs][L1][L0] complex128, st is
- * [nrhs] (or NULL).  Each right-hand side converges on its own. */
+ * [nrhs] (or NULL).  Each right-hand side converges on its own (own Krylov
+ * scalars and stopping tests, the same stopping rule as sw_mg_solve).  On an
+ * SW_MG_FP64 hierarchy the solves run one after the other.  On an SW_MG_MIXED
+ * hierarchy up to 16 right-hand sides advance together through the K-cycle
+ * and the coarsest-level solves of all of them run in one batched kernel that
+ * reads the coarsest stencil once per batch, in FP32 (stencil products and
+ * their sums; iterates and Krylov scalars FP64); the outer FGCR stays FP64.
+ * A right-hand side's result does not depend on the others in its batch.
+ * Returns SW_ERR_NOCONV if any right-hand side did not converge. */
 int sw_mg_solve_batch(sw_mg* mg, int nrhs, const void* B, void* X, double tol, int on_device,
                       sw_solve_stats* st);
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <new>
 
@@ -464,15 +465,63 @@ int sw_mg_solve_batch(sw_mg* mg, int nrhs, const void* B, void* X, double tol, i
                       sw_solve_stats* st) {
   if (!mg || !B || !X || nrhs < 0) return SW_ERR_ARG;
   size_t N = mg->g->N;
-  int worst = SW_OK;
-  for (int k = 0; k < nrhs; ++k) {
-    const double* b = (const double*)B + 2 * N * k;
-    double* x = (double*)X + 2 * N * k;
-    int rc = sw_mg_solve(mg, b, x, tol, on_device, st ? st + k : nullptr);
-    if (rc != SW_OK && rc != SW_ERR_NOCONV) return rc;
-    if (rc != SW_OK) worst = rc;
+  if (!mg->mixed || mg->fine_D) {  // FP64 hierarchies: one solve after the other
+    int worst = SW_OK;
+    for (int k = 0; k < nrhs; ++k) {
+      const double* b = (const double*)B + 2 * N * k;
+      double* x = (double*)X + 2 * N * k;
+      int rc = sw_mg_solve(mg, b, x, tol, on_device, st ? st + k : nullptr);
+      if (rc != SW_OK && rc != SW_ERR_NOCONV) return rc;
+      if (rc != SW_OK) worst = rc;
+    }
+    return worst;
   }
-  return worst;
+  sw_ctx* c = mg->ctx;
+  return guarded(c, [&] {
+    SW_REQUIRE(tol > 0.0 && std::isfinite(tol), SW_ERR_ARG, "tol must be > 0");
+    cudaStream_t s = c->stream;
+    int worst = SW_OK;
+    double2 *db = nullptr, *dx = nullptr;
+    if (!on_device) {
+      db = mg_alloc(mg, (long)N * kMaxBatch);
+      dx = mg_alloc(mg, (long)N * kMaxBatch);
+    }
+    try {
+      for (int k0 = 0; k0 < nrhs; k0 += kMaxBatch) {
+        int nb = std::min(kMaxBatch, nrhs - k0);
+        const double2* bb = (const double2*)B + N * k0;
+        double2* xx = (double2*)X + N * k0;
+        if (!on_device) {
+          SW_CUDA(cudaMemcpyAsync(db, bb, N * nb * sizeof(double2), cudaMemcpyHostToDevice, s));
+          bb = db;
+          xx = dx;
+        }
+        int rc = mg_solve_batch_device(mg, nb, bb, xx, tol, st ? st + k0 : nullptr);
+        if (!on_device)
+          SW_CUDA(cudaMemcpyAsync((double2*)X + N * k0, dx, N * nb * sizeof(double2),
+                                  cudaMemcpyDeviceToHost, s));
+        SW_CUDA(cudaStreamSynchronize(s));
+        if (rc != SW_OK) worst = rc;
+      }
+    } catch (...) {
+      if (!on_device) {
+        cudaStreamSynchronize(s);
+        mg->allocs.pop_back();
+        mg->allocs.pop_back();
+        cudaFree(db);
+        cudaFree(dx);
+      }
+      throw;
+    }
+    if (!on_device) {
+      mg->allocs.pop_back();
+      mg->allocs.pop_back();
+      cudaFree(db);
+      cudaFree(dx);
+    }
+    if (worst == SW_ERR_NOCONV) c->err = "a right-hand side reached outer_maxiter";
+    return worst;
+  });
 }
 
 int sw_debug_maps(sw_gauge* g, int a0, int a1, int32_t* eta, int32_t* eps, int32_t* kd_block,

@@ -564,3 +564,409 @@ int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
   }
   return r.converged ? SW_OK : SW_ERR_NOCONV;
 }
+
+// ================================================================ batched solves
+// Several right-hand sides of one mixed-precision hierarchy advance in
+// lockstep through the same K-cycle: every step is issued for each of them
+// in turn (own work vectors, own page of Krylov scalars, own stopping tests),
+// so that all of them reach the coarsest level together and share one
+// batched coarsest CGNE launch, which reads the coarsest stencil once for the
+// whole batch.  A right-hand side that has met a stopping test drops out of
+// the step while the others go on.  Operator scratch (fine S temporaries) is
+// shared: all steps run in order on the one context stream.
+
+namespace {
+
+using Set = std::vector<int>;
+
+inline int page(int r) { return (r + 1) * kSlotPage; }
+
+// Reads the whole slot array back once (every page) after the queued reductions.
+const double2* slots_read_all(sw_ctx* c) {
+  SW_CUDA(cudaMemcpyAsync(c->h_slots, c->slots, kNumSlots * sizeof(double2),
+                          cudaMemcpyDeviceToHost, c->stream));
+  SW_CUDA(cudaStreamSynchronize(c->stream));
+  if (!c->pending.empty()) timing_harvest(c);
+  return c->h_slots;
+}
+
+struct BatchCounters {
+  std::vector<long long> fine, inter_it, inter_solves, coarse_it, coarse_solves;
+  explicit BatchCounters(int nb)
+      : fine(nb, 0), inter_it(nb, 0), inter_solves(nb, 0), coarse_it(nb, 0),
+        coarse_solves(nb, 0) {}
+};
+
+void op_b(sw_mg* mg, int l, int r, const double2* in, double2* out, bool lowp,
+          BatchCounters& bc) {
+  level_op(mg, l, in, out, nullptr, lowp);
+  if (l == 0) bc.fine[r]++;
+}
+
+// MR smoother (zero guess) for each member: x in kx1, residual in kr1.
+void mr_b(sw_mg* mg, int l, const Set& set, const std::vector<const double2*>& b,
+          BatchCounters& bc) {
+  sw_ctx* c = mg->ctx;
+  long n = level_len(mg, l);
+  double om = mg->p.omega;
+  for (int r : set) {
+    LevelWs& W = mg->batch.lv[l][r];
+    blas_zero(c, W.kx1, n);
+    blas_copy(c, W.kr1, b[r], n);
+  }
+  for (int it = 0; it < mg->p.smoother_iters; ++it)
+    for (int r : set) {
+      LevelWs& W = mg->batch.lv[l][r];
+      int sq = slot_base(l) + page(r) + 8, sqq = sq + 1;
+      op_b(mg, l, r, W.kr1, W.kq, true, bc);
+      blas_dot(c, W.kq, W.kr1, n, sq);
+      blas_norm2(c, W.kq, n, sqq);
+      blas_axpy(c, W.kx1, W.kr1, n, coef_ratio(sq, sqq, om));
+      blas_axpy(c, W.kr1, W.kq, n, coef_ratio(sq, sqq, -om));
+    }
+}
+
+void solve_level_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc);
+
+// out_r = M(g_r) on level l for every member of the set.
+void kcycle_b(sw_mg* mg, int l, const Set& set, const std::vector<const double2*>& g,
+              const std::vector<double2*>& out, BatchCounters& bc) {
+  sw_ctx* c = mg->ctx;
+  cudaStream_t s = c->stream;
+  MgLevel& L = mg->lev[l];
+  long n = level_len(mg, l);
+  mr_b(mg, l, set, g, bc);
+  for (int r : set) {
+    LevelWs& W = mg->batch.lv[l][r];
+    LevelWs& CW = mg->batch.lv[l + 1][r];
+    if (l == 0)
+      launch_restrict_fine(mg->g, L.b0, L.b1, L.nv, L.P, W.kr1, CW.rhs, s);
+    else
+      launch_restrict_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, W.kr1, CW.rhs, s);
+  }
+  solve_level_b(mg, l + 1, set, bc);
+  std::vector<const double2*> r2(mg->batch.nb, nullptr);
+  for (int r : set) {
+    LevelWs& W = mg->batch.lv[l][r];
+    LevelWs& CW = mg->batch.lv[l + 1][r];
+    if (l == 0)
+      launch_prolong_fine(mg->g, L.b0, L.b1, L.nv, L.P, CW.sol, W.ke, s);
+    else
+      launch_prolong_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, CW.sol, W.ke, s);
+    op_b(mg, l, r, W.ke, W.kq, true, bc);
+    blas_sub(c, W.kr2, W.kr1, W.kq, n);
+    blas_copy(c, W.kx3, W.kx1, n);  // keep x1 while the post-smoother reuses kx1 / kr1
+    r2[r] = W.kr2;
+  }
+  mr_b(mg, l, set, r2, bc);
+  for (int r : set) {
+    LevelWs& W = mg->batch.lv[l][r];
+    blas_add3(c, out[r], W.kx3, W.ke, W.kx1, n);  // (x1 + e) + x3
+  }
+}
+
+struct SetResult {
+  std::vector<int> it, restarts;
+  std::vector<char> conv;
+};
+
+// Flexible GCR (the steps of fgcr above) for every member of the set.
+SetResult fgcr_b(sw_mg* mg, int l, const Set& set, const std::vector<const double2*>& b,
+                 const std::vector<double2*>& x, const std::vector<double>& tol_abs, int restart,
+                 int maxiter, bool confirm, BatchCounters& bc) {
+  sw_ctx* c = mg->ctx;
+  long n = level_len(mg, l);
+  int nb = mg->batch.nb;
+  SetResult res{std::vector<int>(nb, 0), std::vector<int>(nb, 0), std::vector<char>(nb, 0)};
+  std::vector<int> k(nb, 0);
+  std::vector<char> done(nb, 1);
+  for (int r : set) {
+    LevelWs& W = mg->batch.lv[l][r];
+    blas_zero(c, x[r], n);
+    blas_copy(c, W.gr, b[r], n);
+    done[r] = 0;
+  }
+  const bool lowp = l > 0;
+  for (;;) {
+    Set act;
+    for (int r : set)
+      if (!done[r]) act.push_back(r);
+    if (act.empty()) break;
+    for (int r : act) blas_norm2(c, mg->batch.lv[l][r].gr, n, slot_base(l) + page(r));
+    const double2* hs = slots_read_all(c);
+    Set cand, go;
+    for (int r : act) {
+      double rn = std::sqrt(hs[slot_base(l) + page(r)].x);
+      check_norm(rn, "batched GCR residual");
+      if (rn <= tol_abs[r]) {
+        if (confirm) {
+          cand.push_back(r);
+        } else {
+          done[r] = 1;
+          res.conv[r] = 1;
+        }
+      } else if (res.it[r] >= maxiter) {
+        done[r] = 1;
+      } else {
+        go.push_back(r);
+      }
+    }
+    if (!cand.empty()) {  // confirm on the true residual, then test everybody again
+      for (int r : cand) {
+        LevelWs& W = mg->batch.lv[l][r];
+        op_b(mg, l, r, x[r], W.gtmp, lowp, bc);
+        blas_sub(c, W.gtmp, b[r], W.gtmp, n);
+        blas_norm2(c, W.gtmp, n, slot_base(l) + page(r) + 1);
+      }
+      const double2* hs2 = slots_read_all(c);
+      for (int r : cand) {
+        double rt = std::sqrt(hs2[slot_base(l) + page(r) + 1].x);
+        check_norm(rt, "batched GCR true residual");
+        if (rt <= tol_abs[r]) {
+          done[r] = 1;
+          res.conv[r] = 1;
+        } else {
+          LevelWs& W = mg->batch.lv[l][r];
+          blas_copy(c, W.gr, W.gtmp, n);
+          k[r] = 0;
+          res.restarts[r]++;
+        }
+      }
+      continue;
+    }
+    if (go.empty()) continue;  // every active member has just stopped
+    std::vector<const double2*> g(nb, nullptr);
+    std::vector<double2*> p(nb, nullptr);
+    for (int r : go) {
+      LevelWs& W = mg->batch.lv[l][r];
+      g[r] = W.gr;
+      p[r] = W.gp[k[r]];
+    }
+    if (l + 1 < mg->nlev)
+      kcycle_b(mg, l, go, g, p, bc);
+    else
+      for (int r : go) blas_copy(c, p[r], g[r], n);
+    for (int r : go) {
+      LevelWs& W = mg->batch.lv[l][r];
+      int sb = slot_base(l) + page(r);
+      int s_qq = sb + 2, s_a = sb + 3, s_b = sb + 4;
+      double2* q = W.gq[k[r]];
+      double2* pr = W.gp[k[r]];
+      op_b(mg, l, r, pr, q, lowp, bc);
+      for (int j = 0; j < k[r]; ++j) {
+        blas_dot(c, W.gq[j], q, n, s_b);
+        blas_axpy(c, q, W.gq[j], n, coef_ratio(s_b, -1, -1.0));
+        blas_axpy(c, pr, W.gp[j], n, coef_ratio(s_b, -1, -1.0));
+      }
+      blas_norm2(c, q, n, s_qq);
+      blas_scale(c, q, n, coef_ratio(-1, s_qq, 1.0, COEF_SQRT_DEN));
+      blas_scale(c, pr, n, coef_ratio(-1, s_qq, 1.0, COEF_SQRT_DEN));
+      blas_dot(c, q, W.gr, n, s_a);
+      blas_axpy(c, x[r], pr, n, coef_ratio(s_a, -1, 1.0));
+      blas_axpy(c, W.gr, q, n, coef_ratio(s_a, -1, -1.0));
+      ++k[r];
+      ++res.it[r];
+      if (k[r] == restart && res.it[r] < maxiter) {
+        op_b(mg, l, r, x[r], W.gtmp, lowp, bc);
+        blas_sub(c, W.gr, b[r], W.gtmp, n);
+        k[r] = 0;
+        res.restarts[r]++;
+      }
+    }
+  }
+  return res;
+}
+
+void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
+  if (set.empty()) return;
+  sw_ctx* c = mg->ctx;
+  MgLevel& L = mg->lev[l];
+  BatchWs& B = mg->batch;
+  int nb = (int)set.size();
+  double2* hp[32] = {nullptr};
+  for (int i = 0; i < nb; ++i) {
+    hp[i] = B.lv[l][set[i]].rhs;
+    hp[16 + i] = B.lv[l][set[i]].sol;
+  }
+  SW_CUDA(cudaMemcpyAsync(B.dptr, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));
+  SW_CUDA(cudaStreamSynchronize(c->stream));  // hp is a host stack array
+  std::lock_guard<std::mutex> lock(g_persistent_mutex);
+  int tk = timing_begin(c, kCatCgne);
+  bool ran = launch_cgne_batch(CoarseGeom{L.E0, L.E1, L.nc}, B.Yf, nb, B.dptr, B.dptr + 16, B.X,
+                               B.R, B.P, B.Rf, B.Pf, B.partials, B.bar, B.status,
+                               mg->p.coarsest_maxiter, mg->p.coarsest_tol, c->device, c->stream);
+  timing_end(c, tk);
+  if (!ran)
+    throw SwError{SW_ERR_ARG, "no batched coarsest solver for nc = " + std::to_string(L.nc)};
+  int hst[18];
+  SW_CUDA(cudaMemcpyAsync(hst, B.status, sizeof(hst), cudaMemcpyDeviceToHost, c->stream));
+  SW_CUDA(cudaStreamSynchronize(c->stream));
+  if (!c->pending.empty()) timing_harvest(c);
+  if (hst[0]) throw SwError{SW_ERR_TIMEOUT, "batched coarsest CGNE: a grid barrier wait gave up"};
+  if (hst[1]) throw SwError{SW_ERR_NAN, "non-finite norm in batched CGNE"};
+  for (int i = 0; i < nb; ++i) {
+    bc.coarse_it[set[i]] += hst[2 + i];
+    bc.coarse_solves[set[i]]++;
+    if (c->timing) c->t_count[kCatCgne + 1] += hst[2 + i];
+  }
+}
+
+void solve_level_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
+  sw_ctx* c = mg->ctx;
+  if (l == mg->nlev - 1) {
+    cgne_b(mg, l, set, bc);
+    return;
+  }
+  long n = level_len(mg, l);
+  int nb = mg->batch.nb;
+  for (int r : set) blas_norm2(c, mg->batch.lv[l][r].rhs, n, slot_base(l) + page(r) + 5);
+  const double2* hs = slots_read_all(c);
+  std::vector<double> tol(nb, 0.0);
+  std::vector<const double2*> b(nb, nullptr);
+  std::vector<double2*> x(nb, nullptr);
+  for (int r : set) {
+    double bn = std::sqrt(hs[slot_base(l) + page(r) + 5].x);
+    check_norm(bn, "batched intermediate right-hand side");
+    tol[r] = mg->p.inter_tol * bn;
+    b[r] = mg->batch.lv[l][r].rhs;
+    x[r] = mg->batch.lv[l][r].sol;
+  }
+  SetResult res =
+      fgcr_b(mg, l, set, b, x, tol, mg->p.inter_restart, mg->p.inter_maxiter, false, bc);
+  for (int r : set) {
+    bc.inter_it[r] += res.it[r];
+    bc.inter_solves[r]++;
+  }
+}
+
+void batch_alloc(sw_mg* mg) {
+  BatchWs& B = mg->batch;
+  if (B.nb) return;
+  long N = mg->g->N;
+  B.lv.assign(mg->nlev, std::vector<LevelWs>(kMaxBatch));
+  for (int l = 0; l < mg->nlev; ++l) {
+    long n = level_len(mg, l);
+    bool last = l == mg->nlev - 1;
+    int nbas = last ? 0 : (l == 0 ? mg->p.outer_restart : mg->p.inter_restart);
+    for (int r = 0; r < kMaxBatch; ++r) {
+      LevelWs& W = B.lv[l][r];
+      W.rhs = mg_alloc(mg, n);
+      W.sol = mg_alloc(mg, n);
+      if (last) continue;
+      W.gr = mg_alloc(mg, n);
+      W.gtmp = mg_alloc(mg, n);
+      W.gp.assign(nbas, nullptr);
+      W.gq.assign(nbas, nullptr);
+      for (int k = 0; k < nbas; ++k) {
+        W.gp[k] = mg_alloc(mg, n);
+        W.gq[k] = mg_alloc(mg, n);
+      }
+      W.kx1 = mg_alloc(mg, n); W.kr1 = mg_alloc(mg, n); W.kq = mg_alloc(mg, n);
+      W.ke = mg_alloc(mg, n); W.kr2 = mg_alloc(mg, n); W.kx3 = mg_alloc(mg, n);
+    }
+  }
+  MgLevel& C = mg->lev[mg->nlev - 1];
+  long nc = C.ndof;
+  B.X = mg_alloc(mg, nc * kMaxBatch);
+  B.R = mg_alloc(mg, nc * kMaxBatch);
+  B.P = mg_alloc(mg, nc * kMaxBatch);
+  B.Rf = (float2*)mg_alloc(mg, (nc * kMaxBatch + 1) / 2);
+  B.Pf = (float2*)mg_alloc(mg, (nc * kMaxBatch + 1) / 2);
+  long ysz = (long)C.E0 * C.E1 * 5 * C.nc * C.nc;
+  B.Yf = (float2*)mg_alloc(mg, (ysz + 1) / 2);
+  launch_to_f32(C.Y, B.Yf, ysz, mg->ctx->stream);
+  int sms = 0;
+  SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mg->ctx->device));
+  B.partials = (double*)mg_alloc(mg, (long)kMaxBatch * sms);  // 2 phases x 16 x SMs doubles
+  B.bar = (unsigned*)mg_alloc(mg, 1);
+  B.status = (int*)mg_alloc(mg, 5);
+  B.dptr = (double2**)mg_alloc(mg, 16);
+  B.bps = mg_alloc(mg, N * kMaxBatch);
+  B.xps = mg_alloc(mg, N * kMaxBatch);
+  B.lex = mg_alloc(mg, N * kMaxBatch);
+  B.nb = kMaxBatch;
+}
+
+}  // namespace
+
+int mg_solve_batch_device(sw_mg* mg, int nb, const double2* Bl, double2* Xl, double tol,
+                          sw_solve_stats* st) {
+  sw_ctx* c = mg->ctx;
+  sw_gauge* g = mg->g;
+  cudaStream_t s = c->stream;
+  SW_REQUIRE(nb >= 1 && nb <= kMaxBatch, SW_ERR_ARG, "batch of 1..16 right-hand sides");
+  SW_REQUIRE(mg->mixed && !mg->fine_D, SW_ERR_ARG, "batched solves need a mixed hierarchy");
+  auto t0 = std::chrono::steady_clock::now();
+  batch_alloc(mg);
+  BatchWs& B = mg->batch;
+  long N = g->N, half = N / 2;
+  MgLevel& L = mg->lev[0];
+  for (int r = 0; r < nb; ++r) {
+    launch_pack(g, Bl + (long)r * N, B.bps + (long)r * N, s);
+    blas_norm2(c, B.bps + (long)r * N, N, slot_base(0) + page(r) + 40);
+  }
+  const double2* hs = slots_read_all(c);
+  std::vector<double> bn(nb), tol_abs(nb);
+  Set all;
+  for (int r = 0; r < nb; ++r) {
+    bn[r] = std::sqrt(hs[slot_base(0) + page(r) + 40].x);
+    check_norm(bn[r], "right-hand side");
+    tol_abs[r] = tol * bn[r];
+    if (bn[r] > 0.0) all.push_back(r);
+  }
+  std::vector<const double2*> bt(kMaxBatch, nullptr);
+  std::vector<double2*> z(kMaxBatch, nullptr);
+  for (int r = 0; r < nb; ++r) {
+    double2* bps = B.bps + (long)r * N;
+    LevelWs& W = B.lv[0][r];
+    // b~_e = b_e - C_eo B_o^-1 b_o
+    launch_block_apply(g, mg->binv, 1, 0, bps + half, L.stmp + half, s);
+    launch_hop(g, 0, -1.0, bps, L.stmp + half, W.rhs, s);
+    bt[r] = W.rhs;
+    z[r] = W.sol;
+  }
+  BatchCounters bc(kMaxBatch);
+  SetResult res = fgcr_b(mg, 0, all, bt, z, tol_abs, mg->p.outer_restart, mg->p.outer_maxiter,
+                         true, bc);
+  for (int r = 0; r < nb; ++r) {
+    double2* x = Xl + (long)r * N;
+    if (bn[r] == 0.0) {
+      blas_zero(c, x, N);
+      continue;
+    }
+    double2* bps = B.bps + (long)r * N;
+    double2* xps = B.xps + (long)r * N;
+    LevelWs& W = B.lv[0][r];
+    // z_o = b_o - C_oe B_e^-1 z_e ; x = B^-1 z
+    launch_block_apply(g, mg->binv, 0, 0, W.sol, L.stmp, s);
+    launch_hop(g, 1, -1.0, bps + half, L.stmp, L.stmp + half, s);
+    launch_block_apply(g, mg->binv, 0, 0, W.sol, xps, s);
+    launch_block_apply(g, mg->binv, 1, 0, L.stmp + half, xps + half, s);
+    launch_unpack(g, xps, x, s);
+    double2* t = B.lex + (long)r * N;
+    launch_dslash_lex(g, mg->mass, 0, x, t, s);
+    blas_sub(c, t, Bl + (long)r * N, t, N);
+    blas_norm2(c, t, N, slot_base(0) + page(r) + 41);
+  }
+  const double2* hs2 = slots_read_all(c);
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  bool ok = true;
+  for (int r = 0; r < nb; ++r) {
+    bool conv = bn[r] == 0.0 || res.conv[r];
+    ok = ok && conv;
+    if (!st) continue;
+    sw_solve_stats& o = st[r];
+    std::memset(&o, 0, sizeof(o));
+    o.converged = conv ? 1 : 0;
+    o.outer_iters = res.it[r];
+    o.restarts = res.restarts[r];
+    o.fine_applies = bc.fine[r];
+    o.inter_iters = bc.inter_it[r];
+    o.inter_solves = bc.inter_solves[r];
+    o.coarsest_iters = bc.coarse_it[r];
+    o.coarsest_solves = bc.coarse_solves[r];
+    o.true_resid = bn[r] > 0.0 ? std::sqrt(hs2[slot_base(0) + page(r) + 41].x) / bn[r] : 0.0;
+    o.seconds = secs;
+  }
+  return ok ? SW_OK : SW_ERR_NOCONV;
+}

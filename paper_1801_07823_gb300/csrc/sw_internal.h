@@ -64,7 +64,9 @@ __device__ __forceinline__ double2 coef_eval(const double2* S, Coef c) {
   return v;
 }
 
-constexpr int kNumSlots = 320;  // 64 per multigrid level (up to 4), 64 for other solvers
+constexpr int kSlotPage = 320;  // 64 per multigrid level (up to 4), 64 for other solvers
+constexpr int kMaxBatch = 16;   // right-hand sides solved together by sw_mg_solve_batch
+constexpr int kNumSlots = kSlotPage * (kMaxBatch + 1);  // page 0: single solves; 1..16: batch
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so every sum has one order
 
 // Per-category kernel timing with CUDA events on the context stream.
@@ -216,6 +218,16 @@ bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const 
                             double2* x, double2* r, double2* p, float4* rdf, float4* pdf,
                             double* partials, unsigned* bar, int* status, int maxit, double tol,
                             int device, cudaStream_t s, int stall_test = 0);
+
+// Batched coarsest CGNE (batch_cgne.cu): nb <= 16 right-hand sides, FP32
+// stencil Yf, FP64 iterates.  X, R, P: [n][K] double2, Rf, Pf: [n][K] float2,
+// K = cgne_batch_width(nb); partials: 2 K SMs doubles; status: 18 ints
+// ([0] timeout, [1] non-finite, [2 + r] iterations).
+int cgne_batch_width(int nb);
+bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, int nb, const double2* const* b,
+                       double2* const* x, double2* X, double2* R, double2* P, float2* Rf,
+                       float2* Pf, double* partials, unsigned* bar, int* status, int maxit,
+                       double tol, int device, cudaStream_t s);
 
 // ------------------------------------------------------------- mixed.cu
 void fine_apply_S32(const sw_gauge* g, const float2* W32, const float2* binv32,

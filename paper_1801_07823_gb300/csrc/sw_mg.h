@@ -29,6 +29,28 @@ struct MgLevel {
   double2* stmp = nullptr;  // [N] scratch of the fine operators (level 0)
 };
 
+// Work vectors of one right-hand side on one level in a batched solve.
+struct LevelWs {
+  double2 *rhs = nullptr, *sol = nullptr, *gr = nullptr, *gtmp = nullptr;
+  std::vector<double2*> gp, gq;
+  double2 *kx1 = nullptr, *kr1 = nullptr, *kq = nullptr, *ke = nullptr, *kr2 = nullptr;
+  double2 *kx3 = nullptr;
+};
+
+// Workspace of batched solves (allocated on the first one).
+struct BatchWs {
+  int nb = 0;                            // right-hand sides the workspace holds
+  std::vector<std::vector<LevelWs>> lv;  // [level][rhs]
+  double2 *X = nullptr, *R = nullptr, *P = nullptr;  // coarsest CGNE, [n][K]
+  float2 *Rf = nullptr, *Pf = nullptr;
+  float2* Yf = nullptr;                  // FP32 copy of the coarsest stencil
+  double* partials = nullptr;
+  unsigned* bar = nullptr;
+  int* status = nullptr;
+  double2** dptr = nullptr;              // device arrays of b and x pointers, [2][16]
+  double2 *bps = nullptr, *xps = nullptr, *lex = nullptr;  // [16][N] fine buffers
+};
+
 struct sw_mg {
   sw_ctx* ctx = nullptr;
   sw_gauge* g = nullptr;
@@ -47,6 +69,7 @@ struct sw_mg {
   std::vector<double2*> allocs;
   double2 *bps = nullptr, *xps = nullptr, *lexb = nullptr, *lexx = nullptr, *lext = nullptr;
   std::vector<int> setup_iters;
+  BatchWs batch;
   long long st_fine_applies = 0, st_inter_iters = 0, st_inter_solves = 0;
   long long st_coarsest_iters = 0, st_coarsest_solves = 0;
 };
@@ -60,3 +83,8 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed);
 int mg_coarsest_solve(sw_mg* mg, const double2* b, double2* x);  // CGNE on the coarsest level
 int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
                     sw_solve_stats* st);
+// nb (<= 16) right-hand sides of a mixed-precision hierarchy in lockstep, the
+// coarsest solves of all of them in one batched kernel.  B, X: [nb][N]
+// lexicographic device buffers; st: [nb] or NULL.
+int mg_solve_batch_device(sw_mg* mg, int nb, const double2* B, double2* X, double tol,
+                          sw_solve_stats* st);

@@ -372,3 +372,34 @@ def test_galerkin_mg_of_D_negative_control(sw, ctx):
     assert res[sw.SW_MG_COARSEN_D]["true_resid"] > 0.1 and sd["true_resid"] > 0.1
     assert abs(np.log(res[sw.SW_MG_COARSEN_D]["true_resid"] / sd["true_resid"])) < np.log(1.5)
     g.free()
+
+
+def test_batched_solves(sw, mixed64):
+    """sw_mg_solve_batch on a mixed hierarchy: right-hand sides advance together
+    and share batched coarsest solves; each converges to the same 1e-10 true
+    residual (oracle D) with iteration counts close to its single solve, and a
+    right-hand side's result does not depend on its batch-mates."""
+    L, m, th, hmx = mixed64["L"], mixed64["m"], mixed64["th"], mixed64["hmx"]
+    D = operators.dirac(th, m)
+    B = np.stack([si.gaussian_complex(3000 + k, L * L) for k in range(6)])
+    X = np.zeros_like(B)
+    sts = sw.sw_mg_solve_batch(hmx, B, X, 1e-10)
+    for k in range(6):
+        r = np.linalg.norm(B[k] - D @ X[k]) / np.linalg.norm(B[k])
+        assert sts[k]["converged"] and r <= 1e-10, (k, r)
+        x1 = np.zeros(L * L, dtype=complex)
+        s1 = sw.sw_mg_solve(hmx, B[k], x1, 1e-10)
+        assert abs(sts[k]["outer_iters"] - s1["outer_iters"]) <= 2
+        assert sts[k]["coarsest_solves"] == sts[k]["inter_iters"]
+    X1 = np.zeros((1, L * L), dtype=complex)
+    sw.sw_mg_solve_batch(hmx, B[2:3], X1, 1e-10)
+    assert np.array_equal(X1[0], X[2])
+    # a batch of 16 (the widest kernel) with a zero right-hand side in it
+    B16 = np.stack([si.gaussian_complex(4000 + k, L * L) for k in range(16)])
+    B16[5] = 0
+    X16 = np.zeros_like(B16)
+    sts = sw.sw_mg_solve_batch(hmx, B16, X16, 1e-10)
+    assert np.all(X16[5] == 0) and sts[5]["converged"]
+    for k in (0, 7, 15):
+        assert sts[k]["converged"]
+        assert np.linalg.norm(B16[k] - D @ X16[k]) / np.linalg.norm(B16[k]) <= 1e-10
