@@ -478,11 +478,14 @@ def run_native(args, rank, world, local):
         sw.sw_mg_solve_batch(hm, BB, XB, WORKLOAD["tol"])  # warm-up (allocates the workspace)
         barrier()
         flush.zero_()
+        sw.sw_set_timing(ctx, True)
         e0_.record(stream)
         bt = sw.sw_mg_solve_batch(hm, BB, XB, WORKLOAD["tol"])
         e1_.record(stream)
         barrier()
         bel = e0_.elapsed_time(e1_) / 1e3
+        bk = sw.sw_kernel_times(ctx, 7)
+        sw.sw_set_timing(ctx, False)
         if world > 1:
             tt = torch.tensor([bel], device="cuda")
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -496,6 +499,10 @@ def run_native(args, rank, world, local):
             "outer_iters_max": max(x_["outer_iters"] for x_ in bt),
             "coarsest_avg": float(np.mean([x_["coarsest_iters"] / max(x_["coarsest_solves"], 1)
                                            for x_ in bt])),
+            "coarsest_kernel": {"launches": bk[5][0], "ms": bk[5][1],
+                                "iterations": bk[6][0],
+                                "us_per_iteration": 1e3 * bk[5][1] / max(bk[6][0], 1),
+                                "share": bk[5][1] / (bel * 1e3)},
             "speedup_vs_fp64": (world * nbat / bel) / value}
         hm.free()
         # the paper's comparison solver on the same system: CG on the even/odd

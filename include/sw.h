@@ -265,8 +265,10 @@ int sw_dslash_schur_noalloc(sw_gauge* g, double mass, const void* in, void* out)
  *   context stream bracket every application of a level operator: category 0
  *   = fine Schur operator (3 kernels), category l = coarse stencil of level
  *   l + 1 (1 kernel, also its adjoint), category 5 = the coarsest-level CGNE
- *   when it runs as one persistent kernel (one launch per coarsest solve);
- *   category 6 counts that kernel's CGNE iterations (its ms stay 0).
+ *   when it runs as one persistent kernel (one launch per coarsest solve,
+ *   or per batched coarsest solve of sw_mg_solve_batch); category 6 counts
+ *   that kernel's CGNE iterations (a batched launch counts those of its
+ *   slowest right-hand side; the ms stay 0).
  *   Synchronises the stream.
  * sw_kernel_times: for categories 0 .. n-1, the number of applications that
  *   ran and the summed event durations in ms (host arrays, either may be

@@ -12,6 +12,22 @@
 #include "sw_internal.h"
 #include "sw_mg.h"
 
+void report_stale_error(cudaError_t e) {
+  static std::atomic<int> reported{0};
+  if (reported.fetch_add(1) < 4)
+    std::fprintf(stderr, "libsw: cleared a CUDA error pending from before this call: %s\n",
+                 cudaGetErrorString(e));
+}
+
+void dev_free(void* p, const char* what) {
+  if (!p) return;
+  cudaError_t e = cudaFree(p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    std::fprintf(stderr, "libsw: cudaFree(%s) failed: %s\n", what, cudaGetErrorString(e));
+  }
+}
+
 namespace {
 
 __global__ void k_links(const double* __restrict__ theta, double2* __restrict__ Wlex,
@@ -58,6 +74,10 @@ int guarded(sw_ctx* c, F&& f) {
       c->err.clear();
       SW_CUDA(cudaSetDevice(c->device));
     }
+    // A non-sticky error left by an earlier unchecked runtime call of the
+    // process would otherwise surface at this call's first launch check.
+    cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) report_stale_error(stale);
     return f();
   } catch (const SwError& e) {
     return fail(c, e);
@@ -191,14 +211,14 @@ void sw_context_free(sw_ctx* c) {
     cudaEventDestroy(t.b);
   }
   for (cudaEvent_t e : c->spare) cudaEventDestroy(e);
-  cudaFree(c->slots);
-  cudaFree(c->partials);
-  cudaFree(c->counter);
-  cudaFree(c->flag);
-  cudaFree(c->ctl);
-  cudaFree(c->exec);
-  cudaFree(c->bar);
-  cudaFree(c->cgstat);
+  dev_free(c->slots, "slots");
+  dev_free(c->partials, "partials");
+  dev_free(c->counter, "counter");
+  dev_free(c->flag, "flag");
+  dev_free(c->ctl, "ctl");
+  dev_free(c->exec, "exec");
+  dev_free(c->bar, "bar");
+  dev_free(c->cgstat, "cgstat");
   if (c->h_slots) cudaFreeHost(c->h_slots);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   delete c;
@@ -235,7 +255,7 @@ int sw_gauge_load(sw_ctx* c, int L0, int L1, const double* theta, int on_device,
                                                                 g->W_ps32, L0, L1);
     SW_LAUNCH_CHECK();
     SW_CUDA(cudaStreamSynchronize(c->stream));
-    if (tmp) cudaFree(tmp);
+    dev_free(tmp, "theta staging");
     return SW_OK;
   });
   if (rc != SW_OK) {
@@ -253,14 +273,14 @@ void sw_gauge_free(sw_gauge* g) {
     cudaSetDevice(g->ctx->device);
     if (g->ctx->stream) cudaStreamSynchronize(g->ctx->stream);
   }
-  cudaFree(g->W_lex);
-  cudaFree(g->W_lex32);
-  cudaFree(g->W_ps);
-  cudaFree(g->W_ps32);
-  cudaFree(g->binv);
-  cudaFree(g->W3_lex);
-  cudaFree(g->binv_naik);
-  for (auto& t : g->tmp) cudaFree(t);
+  dev_free(g->W_lex, "W_lex");
+  dev_free(g->W_lex32, "W_lex32");
+  dev_free(g->W_ps, "W_ps");
+  dev_free(g->W_ps32, "W_ps32");
+  dev_free(g->binv, "binv");
+  dev_free(g->W3_lex, "W3_lex");
+  dev_free(g->binv_naik, "binv_naik");
+  for (auto& t : g->tmp) dev_free(t, "gauge scratch");
   delete g;
 }
 
@@ -481,43 +501,27 @@ int sw_mg_solve_batch(sw_mg* mg, int nrhs, const void* B, void* X, double tol, i
     SW_REQUIRE(tol > 0.0 && std::isfinite(tol), SW_ERR_ARG, "tol must be > 0");
     cudaStream_t s = c->stream;
     int worst = SW_OK;
+    ScopedBuffers scratch;  // host-side batches are staged through these
     double2 *db = nullptr, *dx = nullptr;
     if (!on_device) {
-      db = mg_alloc(mg, (long)N * kMaxBatch);
-      dx = mg_alloc(mg, (long)N * kMaxBatch);
+      db = scratch.get((long)N * kMaxBatch);
+      dx = scratch.get((long)N * kMaxBatch);
     }
-    try {
-      for (int k0 = 0; k0 < nrhs; k0 += kMaxBatch) {
-        int nb = std::min(kMaxBatch, nrhs - k0);
-        const double2* bb = (const double2*)B + N * k0;
-        double2* xx = (double2*)X + N * k0;
-        if (!on_device) {
-          SW_CUDA(cudaMemcpyAsync(db, bb, N * nb * sizeof(double2), cudaMemcpyHostToDevice, s));
-          bb = db;
-          xx = dx;
-        }
-        int rc = mg_solve_batch_device(mg, nb, bb, xx, tol, st ? st + k0 : nullptr);
-        if (!on_device)
-          SW_CUDA(cudaMemcpyAsync((double2*)X + N * k0, dx, N * nb * sizeof(double2),
-                                  cudaMemcpyDeviceToHost, s));
-        SW_CUDA(cudaStreamSynchronize(s));
-        if (rc != SW_OK) worst = rc;
-      }
-    } catch (...) {
+    for (int k0 = 0; k0 < nrhs; k0 += kMaxBatch) {
+      int nb = std::min(kMaxBatch, nrhs - k0);
+      const double2* bb = (const double2*)B + N * k0;
+      double2* xx = (double2*)X + N * k0;
       if (!on_device) {
-        cudaStreamSynchronize(s);
-        mg->allocs.pop_back();
-        mg->allocs.pop_back();
-        cudaFree(db);
-        cudaFree(dx);
+        SW_CUDA(cudaMemcpyAsync(db, bb, N * nb * sizeof(double2), cudaMemcpyHostToDevice, s));
+        bb = db;
+        xx = dx;
       }
-      throw;
-    }
-    if (!on_device) {
-      mg->allocs.pop_back();
-      mg->allocs.pop_back();
-      cudaFree(db);
-      cudaFree(dx);
+      int rc = mg_solve_batch_device(mg, nb, bb, xx, tol, st ? st + k0 : nullptr);
+      if (!on_device)
+        SW_CUDA(cudaMemcpyAsync((double2*)X + N * k0, dx, N * nb * sizeof(double2),
+                                cudaMemcpyDeviceToHost, s));
+      SW_CUDA(cudaStreamSynchronize(s));
+      if (rc != SW_OK) worst = rc;
     }
     if (worst == SW_ERR_NOCONV) c->err = "a right-hand side reached outer_maxiter";
     return worst;
@@ -598,9 +602,10 @@ int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const voi
     cudaStream_t s = mg->ctx->stream;
     sw_gauge* g = mg->g;
     size_t n = level == 1 ? (size_t)g->N : (size_t)L.ndof;
-    double2* a = mg_alloc(mg, n);
-    double2* b = mg_alloc(mg, n);
-    double2* t = mg_alloc(mg, n);
+    ScopedBuffers scratch;
+    double2* a = scratch.get(n);
+    double2* b = scratch.get(n);
+    double2* t = scratch.get(n);
     SW_CUDA(cudaMemcpyAsync(a, in, n * sizeof(double2),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     if (level == 1) {
@@ -633,10 +638,6 @@ int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const voi
     SW_CUDA(cudaMemcpyAsync(out, b, n * sizeof(double2),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     SW_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < 3; ++k) mg->allocs.pop_back();
-    cudaFree(a);
-    cudaFree(b);
-    cudaFree(t);
     return SW_OK;
   });
 }
@@ -651,9 +652,10 @@ int sw_mg_transfer(sw_mg* mg, int level, int dir, const void* in, void* out, int
     sw_gauge* g = mg->g;
     size_t nf = L.ndof, nc = C.ndof;
     size_t nin = dir == 0 ? nf : nc, nout = dir == 0 ? nc : nf;
-    double2* a = mg_alloc(mg, nin);
-    double2* b = mg_alloc(mg, nout);
-    double2* t = mg_alloc(mg, nf);
+    ScopedBuffers scratch;
+    double2* a = scratch.get(nin);
+    double2* b = scratch.get(nout);
+    double2* t = scratch.get(nf);
     SW_CUDA(cudaMemcpyAsync(a, in, nin * sizeof(double2),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     if (level == 1) {
@@ -675,10 +677,6 @@ int sw_mg_transfer(sw_mg* mg, int level, int dir, const void* in, void* out, int
     SW_CUDA(cudaMemcpyAsync(out, b, nout * sizeof(double2),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     SW_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < 3; ++k) mg->allocs.pop_back();
-    cudaFree(a);
-    cudaFree(b);
-    cudaFree(t);
     return SW_OK;
   });
 }

@@ -4,26 +4,60 @@
 // Same iteration as the single-RHS kernel (cgne.cu) for every right-hand side,
 // each with its own alpha, beta, stopping test and iteration count; a
 // right-hand side that has stopped is no longer updated while the others go
-// on.  The stencil is read once per batch: a lane owns one row for all K
-// right-hand sides, so each FP32 stencil entry feeds K complex products.
-// Stencil products and their sums are FP32 (the coarsest solve of a batch is
-// a 0.2-tolerance preconditioner); the iterates, residuals and Krylov scalars
-// stay FP64, and FP32 copies of r and p feed the stencil.
+// on.
+//
+// A stencil application is a batched block contraction: for every coarse site
+// X, out[X] (nc x K) = sum_d Z[X][d] (nc x nc) v[nb(X, d)] (nc x K), where Z is
+// the forward stencil (A v) or the adjoint stencil (A^dag v).  Both are FP32
+// copies in which each (site, direction) block is one contiguous column-major
+// nc x nc array; the adjoint copy holds Y[nb(X, d)][opp(d)]^dag explicitly, so
+// the two products read their blocks the same way.  A CTA owns the sites
+// X = blockIdx + gridDim * m (m = 0, 1, ...).  One thread copies each
+// (block, neighbour vector) pair into shared memory with bulk asynchronous
+// copies that complete on an mbarrier, a few stages ahead of the threads that
+// use them.  A thread owns one row of a site for four right-hand sides and sums
+// the five blocks' columns in order, so an output is computed the same way for
+// every batch width K.
+//
+// Stencil products and their sums are FP32 (the coarsest solve of a batch is a
+// 0.2-tolerance preconditioner); iterates, residuals and Krylov scalars stay
+// FP64, and FP32 copies of r and p feed the stencil.  Norms are summed per site
+// over its rows in a fixed tree, per CTA over its sites in order, and over the
+// CTAs in a fixed order with one CTA per SM for every K, so a right-hand side's
+// scalars, and hence its result, do not depend on its batch-mates.
 //
 // Layout inside the kernel: right-hand-side-minor, element (dof, rhs) at
-// dof * K + rhs, so the K values a stencil column needs are contiguous.  The
-// grid is one CTA per SM for every batch width and each thread takes the same
-// dofs and rows whatever K is, so a right-hand side's sums run in the same
-// order whatever its batch-mates are: its result does not depend on them.
+// dof * K + rhs, so a neighbour's nc x K vector block is contiguous.
 #include <string>
 
 #include "sw_internal.h"
 
 namespace {
 
-constexpr long kSpinLimit = 1L << 24;
-constexpr int kWarps = 8;
-constexpr int kRows = 8;
+constexpr long kSpinLimit = 1L << 24;      // grid barrier polls
+constexpr long kCopySpinLimit = 1L << 22;  // mbarrier polls per stage
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// Tiling of one batch width: kS sites in flight per CTA, kStages stages of
+// kS (block, vector) pairs each in dynamic shared memory.
+template <int NC, int K>
+struct Tile {
+  static constexpr int kGroups = K / 4;              // four right-hand sides per thread
+  static constexpr int kTps = NC * kGroups;          // threads per site
+  static constexpr int kSiteF2 = NC * NC + NC * K;   // float2 per site and stage
+  static constexpr int kSThr = kThreads / kTps;
+  static constexpr int kSMem0 = (72 * 1024) / (kSiteF2 * 8);
+  static constexpr int kSMem = kSMem0 > 0 ? kSMem0 : 1;
+  static constexpr int kS = kSThr < kSMem ? kSThr : kSMem;
+  static constexpr int kStageF2 = kS * kSiteF2;
+  static constexpr int kStagesMem = (200 * 1024) / (kStageF2 * 8);
+  static constexpr int kStages = kStagesMem < 4 ? kStagesMem : 4;
+  static constexpr int kSmem = kStages * kStageF2 * 8;
+  static_assert(NC % 4 == 0 && K % 4 == 0, "rows and right-hand sides in fours");
+  static_assert(kTps <= kThreads && kS >= 1 && kStages >= 2, "tile does not fit");
+  static_assert(kS * K * 4 <= kThreads, "per-site norm tree needs four threads per pair");
+};
 
 __device__ __forceinline__ int nbr(int X, int d, int E0, int E1) {
   int X0 = X % E0, X1 = X / E0;
@@ -37,8 +71,58 @@ __device__ __forceinline__ int opp(int d) {
   return d == 0 ? 0 : (d == 1 ? 2 : (d == 2 ? 1 : (d == 3 ? 4 : 3)));
 }
 
+// ------------------------------------------------ mbarrier and bulk copies
+__device__ __forceinline__ unsigned su32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false when it gave up.
+__device__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  for (long k = 0; k < kCopySpinLimit; ++k)
+    if (mbar_test(b, parity)) return true;
+  return false;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+// completing as transaction bytes on mbarrier b.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(b))
+      : "memory");
+}
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
 struct BatchArgs {
-  const float2* Y;         // FP32 copy of the coarsest stencil (column-major blocks)
+  const float2* Yf;        // forward stencil blocks (FP32, column-major per (site, direction))
+  const float2* Yd;        // adjoint stencil blocks, same layout
   const double2* const* b; // [K] right-hand sides (entries beyond nb unused)
   double2* const* xout;    // [K] solutions
   double2* X;              // [n][K] FP64 iterates
@@ -48,13 +132,16 @@ struct BatchArgs {
   float2* Pf;
   double* partials;        // [2][K][gridDim.x]
   unsigned* bar;           // grid barrier state (2 words)
-  int* status;             // [0] barrier timeout, [1] non-finite, [2 + r] iterations of rhs r
+  int* status;             // [0] wait timeout or misaligned buffer, [1] non-finite,
+                           // [2 + r] iterations
   int nb, E0, E1, maxit;
   double tol;
 };
 
 __device__ bool grid_barrier(unsigned* bar, int* status) {
   __shared__ int ok;
+  // this thread's generic writes of the phase before the next phase's bulk reads
+  fence_async_global();
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = bar + 1;
@@ -113,74 +200,212 @@ __device__ void grid_sums(const double* part, double* out) {
   __syncthreads();
 }
 
-// Row i of (A v) or (A^dag v) for all K right-hand sides (FP32), summed over
-// the 4 lanes of the row (lane q takes columns [q nc/4, (q+1) nc/4) of all
-// five blocks); every lane of the row holds the totals.
+// acc += y v for one complex product, FP32 (same operation order for every row).
+__device__ __forceinline__ void cmac(float2& acc, float2 y, float vx, float vy) {
+  acc.x = fmaf(y.x, vx, acc.x);
+  acc.x = fmaf(-y.y, vy, acc.x);
+  acc.y = fmaf(y.x, vy, acc.y);
+  acc.y = fmaf(y.y, vx, acc.y);
+}
+
+enum { kModeInit = 0, kModeXR = 1, kModeP = 2 };
+
+// Shared state of the kernel beyond the stage buffers.
 template <int NC, int K>
-__device__ __forceinline__ void stencil_row_b(const float2* __restrict__ Y,
-                                              const float2* __restrict__ v, int X, int i, int q,
-                                              int E0, int E1, bool dagger, float2* acc) {
-  constexpr int QJ = NC / 4;
-  const int j0 = q * QJ;
+struct Smem {
+  unsigned long long full[Tile<NC, K>::kStages];
+  double sq[Tile<NC, K>::kS * K * NC];  // per-row squared norms of the sites in flight
+  double siteval[Tile<NC, K>::kS * K];  // per-site sums
+  double cta_sum[K];                    // this CTA's sum over its sites, in order
+  double red[K][kWarps];
+  double sum[K], rr[K], stop[K], coef[K];
+  int state[K];                         // 0 active, 1 stopped, 2 non-finite
+  int iters[K];
+  int any;
+  int copy_timeout;
+};
+
+// One stencil application over this CTA's sites fused with the update of its
+// mode, leaving this CTA's per-right-hand-side norm sum in sm.cta_sum:
+//   kModeInit: p = A^dag r (all right-hand sides), |p|^2
+//   kModeXR:   w = A p; x += alpha p; r -= alpha w (active ones), |r|^2
+//   kModeP:    p = A^dag r + beta p (active ones), |p|^2
+// qbase counts the stages this CTA has used so far (buffer and mbarrier parity).
+template <int NC, int K, int MODE>
+__device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm,
+                              unsigned& qbase) {
+  using T = Tile<NC, K>;
+  const int t = threadIdx.x;
+  const int s = t / T::kTps, w = t - s * T::kTps;
+  const int g = w % T::kGroups, i = w / T::kGroups;
+  const bool act = s < T::kS;
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int nsites = a.E0 * a.E1;
+  const int nmine = cta < nsites ? (nsites - 1 - cta) / G + 1 : 0;
+  const int nchunks = (nmine + T::kS - 1) / T::kS;
+  const int nst = nchunks * 5;
+  const float2* Z = MODE == kModeXR ? a.Yf : a.Yd;
+  const float2* V = MODE == kModeXR ? a.Pf : a.Rf;
+
+  // stage q of this phase: chunk q / 5 of this CTA's sites, direction q % 5
+  auto issue = [&](int q) {
+    const int c = q / 5, d = q - c * 5;
+    const unsigned Q = qbase + q;
+    float2* buf = stage + (size_t)(Q % T::kStages) * T::kStageF2;
+    unsigned long long* mb = sm.full + Q % T::kStages;
+    const int nv = min(T::kS, nmine - c * T::kS);
+    mbar_arrive_expect(mb, (unsigned)(nv * T::kSiteF2 * 8));
+    for (int ss = 0; ss < nv; ++ss) {
+      const int Xs = cta + G * (c * T::kS + ss);
+      const int nbs = nbr(Xs, d, a.E0, a.E1);
+      bulk_load(buf + ss * NC * NC, Z + ((size_t)Xs * 5 + d) * NC * NC, NC * NC * 8, mb);
+      bulk_load(buf + T::kS * NC * NC + ss * NC * K, V + (size_t)nbs * NC * K, NC * K * 8, mb);
+    }
+  };
+
+  if (t == 0) {
+    fence_async_global();  // other CTAs' writes, acquired at the grid barrier, before bulk reads
+    const int pre = nst < T::kStages ? nst : T::kStages;
+    for (int q = 0; q < pre; ++q) issue(q);
+  }
+  if (t < K) sm.cta_sum[t] = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const int m = c * T::kS + s;
+    const bool valid = act && m < nmine;
+    const int X = cta + G * m;
+    float2 acc[4];
 #pragma unroll
-  for (int r = 0; r < K; ++r) acc[r] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int d = 0; d < 5; ++d) {
-    const long nb = nbr(X, d, E0, E1);
-    const long ybase = dagger ? ((nb * 5 + opp(d)) * NC + i) * NC + j0
-                              : (((long)X * 5 + d) * NC + j0) * NC + i;
-    const long ystep = dagger ? 1 : NC;
-    const float2* xb = v + (nb * NC + j0) * K;
-#pragma unroll 2
-    for (int t = 0; t < QJ; ++t) {
-      float2 y = __ldg(Y + ybase + t * ystep);
-      if (dagger) y.y = -y.y;
-      const float4* xv = reinterpret_cast<const float4*>(xb + t * K);
-#pragma unroll
-      for (int r2 = 0; r2 < K / 2; ++r2) {
-        float4 x2 = __ldcg(xv + r2);
-        float2& a0 = acc[2 * r2];
-        float2& a1 = acc[2 * r2 + 1];
-        a0.x = fmaf(y.x, x2.x, a0.x);
-        a0.x = fmaf(-y.y, x2.y, a0.x);
-        a0.y = fmaf(y.x, x2.y, a0.y);
-        a0.y = fmaf(y.y, x2.x, a0.y);
-        a1.x = fmaf(y.x, x2.z, a1.x);
-        a1.x = fmaf(-y.y, x2.w, a1.x);
-        a1.y = fmaf(y.x, x2.w, a1.y);
-        a1.y = fmaf(y.y, x2.z, a1.y);
+    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int d = 0; d < 5; ++d) {
+      const int q = c * 5 + d;
+      const unsigned Q = qbase + q;
+      const int bi = (int)(Q % T::kStages);
+      if (!mbar_wait(sm.full + bi, (Q / T::kStages) & 1u)) {
+        sm.copy_timeout = 1;
+        atomicExch(a.status, 1);
+      }
+      if (valid) {
+        const float2* Ys = stage + (size_t)bi * T::kStageF2 + s * NC * NC + i;
+        const float2* Vs = stage + (size_t)bi * T::kStageF2 + T::kS * NC * NC + s * NC * K + 4 * g;
+#pragma unroll 8
+        for (int j = 0; j < NC; ++j) {
+          const float2 y = Ys[j * NC];
+          const float4 v01 = *reinterpret_cast<const float4*>(Vs + j * K);
+          const float4 v23 = *reinterpret_cast<const float4*>(Vs + j * K + 2);
+          cmac(acc[0], y, v01.x, v01.y);
+          cmac(acc[1], y, v01.z, v01.w);
+          cmac(acc[2], y, v23.x, v23.y);
+          cmac(acc[3], y, v23.z, v23.w);
+        }
+      }
+      __syncthreads();  // every thread is done with this buffer
+      if (t == 0 && q + T::kStages < nst) {
+        fence_async_shared();
+        issue(q + T::kStages);
       }
     }
-  }
+    double q2[4] = {0.0, 0.0, 0.0, 0.0};
+    if (valid) {
+      const size_t e = ((size_t)X * NC + i) * K + 4 * g;
 #pragma unroll
-  for (int r = 0; r < K; ++r) {
-    acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, 1);
-    acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, 1);
-    acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, 2);
-    acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, 2);
+      for (int u = 0; u < 4; ++u) {
+        const int r = 4 * g + u;
+        if (MODE == kModeInit) {
+          const double2 pv = make_double2((double)acc[u].x, (double)acc[u].y);
+          a.P[e + u] = pv;
+          a.Pf[e + u] = acc[u];
+          q2[u] = fma(pv.x, pv.x, pv.y * pv.y);
+        } else if (sm.state[r] == 0) {
+          if (MODE == kModeXR) {
+            const double al = sm.coef[r];
+            const double2 pv = __ldcg(a.P + e + u);
+            double2 xv = __ldcg(a.X + e + u), rv = __ldcg(a.R + e + u);
+            xv.x = fma(al, pv.x, xv.x);
+            xv.y = fma(al, pv.y, xv.y);
+            rv.x = fma(-al, (double)acc[u].x, rv.x);
+            rv.y = fma(-al, (double)acc[u].y, rv.y);
+            a.X[e + u] = xv;
+            a.R[e + u] = rv;
+            a.Rf[e + u] = make_float2((float)rv.x, (float)rv.y);
+            q2[u] = fma(rv.x, rv.x, rv.y * rv.y);
+          } else {
+            const double be = sm.coef[r];
+            double2 pv = __ldcg(a.P + e + u);
+            pv.x = fma(be, pv.x, (double)acc[u].x);
+            pv.y = fma(be, pv.y, (double)acc[u].y);
+            a.P[e + u] = pv;
+            a.Pf[e + u] = make_float2((float)pv.x, (float)pv.y);
+            q2[u] = fma(pv.x, pv.x, pv.y * pv.y);
+          }
+        }
+      }
+    }
+    // per-site sums over rows: four threads per (site, rhs) pair, NC/4 rows each
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sm.sq[(s * K + 4 * g + u) * NC + i] = q2[u];
+    }
+    __syncthreads();
+    {
+      const int pair = t >> 2, part = t & 3;
+      double v = 0.0;
+      if (pair < T::kS * K) {
+        const double* src = sm.sq + pair * NC + part * (NC / 4);
+        for (int k = 0; k < NC / 4; ++k) v += src[k];
+      }
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      if (part == 0 && pair < T::kS * K) sm.siteval[pair] = v;
+    }
+    __syncthreads();
+    if (t < K) {
+      for (int ss = 0; ss < T::kS; ++ss)
+        if (c * T::kS + ss < nmine) sm.cta_sum[t] += sm.siteval[ss * K + t];
+    }
+  }
+  qbase += (unsigned)nst;
+}
+
+// Thread 0 waits once more for the last stages of every buffer after a copy
+// wait gave up, so that no copy is in flight when the CTA exits.
+template <int NC, int K>
+__device__ void drain_copies(Smem<NC, K>& sm, unsigned qbase) {
+  using T = Tile<NC, K>;
+  __syncthreads();
+  if (threadIdx.x == 0 && sm.copy_timeout) {
+    for (unsigned Q = qbase >= (unsigned)T::kStages ? qbase - T::kStages : 0u; Q < qbase; ++Q)
+      mbar_wait(sm.full + Q % T::kStages, (Q / T::kStages) & 1u);
   }
 }
 
 template <int NC, int K>
-__global__ void __launch_bounds__(kWarps * 32, 1) k_cgne_batch(BatchArgs a) {
-  __shared__ double red[K][kWarps];
-  __shared__ double sh_sum[K], sh_rr[K], sh_stop[K], sh_coef[K];
-  __shared__ int sh_state[K];  // 0 active, 1 stopped, 2 non-finite
-  __shared__ int sh_iters[K];
-  __shared__ int sh_any;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rr8 = lane >> 2, q = lane & 3;
-  const int nsites = a.E0 * a.E1;
-  const long n = (long)nsites * NC;
-  const int chunks = NC / kRows;
-  const int nitems = nsites * chunks;
-  const int nwarps = gridDim.x * kWarps;
-  const int rounds = (nitems + nwarps - 1) / nwarps;
+__device__ void publish(Smem<NC, K>& sm, double* part) {
+  if (threadIdx.x < K) {
+    part[threadIdx.x * gridDim.x + blockIdx.x] = sm.cta_sum[threadIdx.x];
+    __threadfence();
+  }
+}
+
+template <int NC, int K>
+__global__ void __launch_bounds__(kThreads, 1) k_cgne_batch(BatchArgs a) {
+  extern __shared__ __align__(128) float2 stage[];
+  __shared__ Smem<NC, K> sm;
+  const long n = (long)a.E0 * a.E1 * NC;
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthr = (long)gridDim.x * blockDim.x;
+  unsigned qbase = 0;
   double nrm[K];
-  float2 acc[K];
 
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < Tile<NC, K>::kStages; ++k) mbar_init(sm.full + k, 1);
+    sm.copy_timeout = 0;
+    fence_mbar_init();
+    fence_async_shared();
+    // bulk copies need 16-byte aligned ends: refuse (status, then every CTA
+    // returns at the first grid barrier, before any copy) rather than issue one
+    const size_t gl = (size_t)a.Yf | (size_t)a.Yd | (size_t)a.Rf | (size_t)a.Pf;
+    if (((su32(stage) & 15u) | (unsigned)(gl & 15)) != 0) atomicExch(a.status, 1);
+  }
   // gather: X = 0, R = b, Rf = float(b), ||r||^2 per right-hand side
 #pragma unroll
   for (int r = 0; r < K; ++r) nrm[r] = 0.0;
@@ -196,129 +421,67 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_cgne_batch(BatchArgs a) {
     }
   }
   int ph = 0;
-  cta_partials<K>(nrm, red, a.partials + ph * K * gridDim.x);
+  cta_partials<K>(nrm, sm.red, a.partials + ph * K * gridDim.x);
   if (!grid_barrier(a.bar, a.status)) return;
-  grid_sums<K>(a.partials + ph * K * gridDim.x, sh_sum);
+  grid_sums<K>(a.partials + ph * K * gridDim.x, sm.sum);
   if (threadIdx.x < K) {
     int r = threadIdx.x;
-    double rr0 = sh_sum[r];
-    sh_rr[r] = rr0;
-    sh_stop[r] = a.tol * sqrt(rr0);
-    sh_iters[r] = 0;
-    sh_state[r] = !isfinite(rr0) ? 2 : ((a.maxit <= 0 || !(sqrt(rr0) > sh_stop[r])) ? 1 : 0);
+    double rr0 = sm.sum[r];
+    sm.rr[r] = rr0;
+    sm.stop[r] = a.tol * sqrt(rr0);
+    sm.iters[r] = 0;
+    sm.state[r] = !isfinite(rr0) ? 2 : ((a.maxit <= 0 || !(sqrt(rr0) > sm.stop[r])) ? 1 : 0);
   }
   __syncthreads();
   ph ^= 1;
   // P = A^dag R, ||p||^2
-#pragma unroll
-  for (int r = 0; r < K; ++r) nrm[r] = 0.0;
-  for (int rd = 0; rd < rounds; ++rd) {
-    int item = rd * nwarps + warp * gridDim.x + blockIdx.x;
-    if (item >= nitems) break;  // warp-uniform
-    int X = item / chunks, i = (item - X * chunks) * kRows + rr8;
-    stencil_row_b<NC, K>(a.Y, a.Rf, X, i, q, a.E0, a.E1, true, acc);
-    if (q == 0) {
-      long e = ((long)X * NC + i) * K;
-#pragma unroll
-      for (int r = 0; r < K; ++r) {
-        double2 w = make_double2((double)acc[r].x, (double)acc[r].y);
-        a.P[e + r] = w;
-        a.Pf[e + r] = acc[r];
-        nrm[r] = fma(w.x, w.x, fma(w.y, w.y, nrm[r]));
-      }
-    }
-  }
-  cta_partials<K>(nrm, red, a.partials + ph * K * gridDim.x);
-  if (!grid_barrier(a.bar, a.status)) return;
-  grid_sums<K>(a.partials + ph * K * gridDim.x, sh_sum);
-  if (threadIdx.x < K) sh_coef[threadIdx.x] = sh_rr[threadIdx.x] / sh_sum[threadIdx.x];  // alpha
+  stencil_phase<NC, K, kModeInit>(a, stage, sm, qbase);
+  publish<NC, K>(sm, a.partials + ph * K * gridDim.x);
+  if (!grid_barrier(a.bar, a.status)) return drain_copies<NC, K>(sm, qbase);
+  grid_sums<K>(a.partials + ph * K * gridDim.x, sm.sum);
+  if (threadIdx.x < K) sm.coef[threadIdx.x] = sm.rr[threadIdx.x] / sm.sum[threadIdx.x];  // alpha
   if (threadIdx.x == 0) {
     int any = 0;
-    for (int r = 0; r < K; ++r) any |= sh_state[r] == 0;
-    sh_any = any;
+    for (int r = 0; r < K; ++r) any |= sm.state[r] == 0;
+    sm.any = any;
   }
   __syncthreads();
   ph ^= 1;
-  while (sh_any) {
-    // P1: w = A p; x += alpha p; r -= alpha w (right-hand sides still active)
-#pragma unroll
-    for (int r = 0; r < K; ++r) nrm[r] = 0.0;
-    for (int rd = 0; rd < rounds; ++rd) {
-      int item = rd * nwarps + warp * gridDim.x + blockIdx.x;
-      if (item >= nitems) break;
-      int X = item / chunks, i = (item - X * chunks) * kRows + rr8;
-      stencil_row_b<NC, K>(a.Y, a.Pf, X, i, q, a.E0, a.E1, false, acc);
-      if (q == 0) {
-        long e = ((long)X * NC + i) * K;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          if (sh_state[r] != 0) continue;
-          double al = sh_coef[r];
-          double2 pv = __ldcg(a.P + e + r), xv = __ldcg(a.X + e + r), rv = __ldcg(a.R + e + r);
-          xv.x = fma(al, pv.x, xv.x);
-          xv.y = fma(al, pv.y, xv.y);
-          rv.x = fma(-al, (double)acc[r].x, rv.x);
-          rv.y = fma(-al, (double)acc[r].y, rv.y);
-          a.X[e + r] = xv;
-          a.R[e + r] = rv;
-          a.Rf[e + r] = make_float2((float)rv.x, (float)rv.y);
-          nrm[r] = fma(rv.x, rv.x, fma(rv.y, rv.y, nrm[r]));
-        }
-      }
-    }
-    cta_partials<K>(nrm, red, a.partials + ph * K * gridDim.x);
-    if (!grid_barrier(a.bar, a.status)) return;
-    grid_sums<K>(a.partials + ph * K * gridDim.x, sh_sum);
+  while (sm.any) {
+    // w = A p; x += alpha p; r -= alpha w (right-hand sides still active)
+    stencil_phase<NC, K, kModeXR>(a, stage, sm, qbase);
+    publish<NC, K>(sm, a.partials + ph * K * gridDim.x);
+    if (!grid_barrier(a.bar, a.status)) return drain_copies<NC, K>(sm, qbase);
+    grid_sums<K>(a.partials + ph * K * gridDim.x, sm.sum);
     if (threadIdx.x < K) {
       int r = threadIdx.x;
-      if (sh_state[r] == 0) {
-        double rr_new = sh_sum[r];
-        int k = ++sh_iters[r];
+      if (sm.state[r] == 0) {
+        double rr_new = sm.sum[r];
+        int k = ++sm.iters[r];
         if (!isfinite(rr_new))
-          sh_state[r] = 2;
-        else if (!(k < a.maxit && sqrt(rr_new) > sh_stop[r]))
-          sh_state[r] = 1;
-        sh_coef[r] = rr_new / sh_rr[r];  // beta
-        sh_rr[r] = rr_new;
+          sm.state[r] = 2;
+        else if (!(k < a.maxit && sqrt(rr_new) > sm.stop[r]))
+          sm.state[r] = 1;
+        sm.coef[r] = rr_new / sm.rr[r];  // beta
+        sm.rr[r] = rr_new;
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       int any = 0;
-      for (int r = 0; r < K; ++r) any |= sh_state[r] == 0;
-      sh_any = any;
+      for (int r = 0; r < K; ++r) any |= sm.state[r] == 0;
+      sm.any = any;
     }
     __syncthreads();
     ph ^= 1;
-    if (!sh_any) break;
-    // P2: p = A^dag r + beta p (right-hand sides still active)
-#pragma unroll
-    for (int r = 0; r < K; ++r) nrm[r] = 0.0;
-    for (int rd = 0; rd < rounds; ++rd) {
-      int item = rd * nwarps + warp * gridDim.x + blockIdx.x;
-      if (item >= nitems) break;
-      int X = item / chunks, i = (item - X * chunks) * kRows + rr8;
-      stencil_row_b<NC, K>(a.Y, a.Rf, X, i, q, a.E0, a.E1, true, acc);
-      if (q == 0) {
-        long e = ((long)X * NC + i) * K;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          if (sh_state[r] != 0) continue;
-          double be = sh_coef[r];
-          double2 pv = __ldcg(a.P + e + r);
-          pv.x = fma(be, pv.x, (double)acc[r].x);
-          pv.y = fma(be, pv.y, (double)acc[r].y);
-          a.P[e + r] = pv;
-          a.Pf[e + r] = make_float2((float)pv.x, (float)pv.y);
-          nrm[r] = fma(pv.x, pv.x, fma(pv.y, pv.y, nrm[r]));
-        }
-      }
-    }
-    cta_partials<K>(nrm, red, a.partials + ph * K * gridDim.x);
-    if (!grid_barrier(a.bar, a.status)) return;
-    grid_sums<K>(a.partials + ph * K * gridDim.x, sh_sum);
-    if (threadIdx.x < K && sh_state[threadIdx.x] == 0)
-      sh_coef[threadIdx.x] = sh_rr[threadIdx.x] / sh_sum[threadIdx.x];  // alpha
+    if (!sm.any) break;
+    // p = A^dag r + beta p (right-hand sides still active)
+    stencil_phase<NC, K, kModeP>(a, stage, sm, qbase);
+    publish<NC, K>(sm, a.partials + ph * K * gridDim.x);
+    if (!grid_barrier(a.bar, a.status)) return drain_copies<NC, K>(sm, qbase);
+    grid_sums<K>(a.partials + ph * K * gridDim.x, sm.sum);
+    if (threadIdx.x < K && sm.state[threadIdx.x] == 0)
+      sm.coef[threadIdx.x] = sm.rr[threadIdx.x] / sm.sum[threadIdx.x];  // alpha
     __syncthreads();
     ph ^= 1;
   }
@@ -326,19 +489,35 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_cgne_batch(BatchArgs a) {
   for (long dof = tid; dof < n; dof += nthr)
     for (int r = 0; r < a.nb; ++r) a.xout[r][dof] = __ldcg(a.X + dof * K + r);
   if (blockIdx.x == 0 && threadIdx.x < K) {
-    if (sh_state[threadIdx.x] == 2) atomicExch(a.status + 1, 1);
-    a.status[2 + threadIdx.x] = sh_iters[threadIdx.x];
+    if (sm.state[threadIdx.x] == 2) atomicExch(a.status + 1, 1);
+    a.status[2 + threadIdx.x] = sm.iters[threadIdx.x];
+  }
+}
+
+// Adjoint blocks: Yd[X][d] = Y[nb(X, d)][opp(d)]^dag in FP32, one CTA per block.
+__global__ void k_adjoint_f32(const double2* __restrict__ Y, float2* __restrict__ Yd, int E0,
+                              int E1, int nc) {
+  const int X = blockIdx.x / 5, d = blockIdx.x - 5 * (blockIdx.x / 5);
+  const size_t src = ((size_t)nbr(X, d, E0, E1) * 5 + opp(d)) * nc * nc;
+  const size_t dst = ((size_t)X * 5 + d) * nc * nc;
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+    const int i = e % nc, j = e / nc;  // (row i, column j) of the adjoint block
+    const double2 y = Y[src + (size_t)i * nc + j];  // (row j, column i) of the neighbour's block
+    Yd[dst + e] = make_float2((float)y.x, (float)-y.y);
   }
 }
 
 template <int NC, int K>
 bool launch_b(const BatchArgs& args, int device, cudaStream_t s) {
+  using T = Tile<NC, K>;
   static int cached_grid[64] = {0};
   int& grid = cached_grid[device & 63];
   if (grid == 0) {
     int occ = 0, sms = 0, coop = 0;
-    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne_batch<NC, K>, kWarps * 32,
-                                                          0));
+    SW_CUDA(cudaFuncSetAttribute((const void*)k_cgne_batch<NC, K>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, T::kSmem));
+    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne_batch<NC, K>, kThreads,
+                                                          T::kSmem));
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     if (!coop || occ < 1)
@@ -350,7 +529,7 @@ bool launch_b(const BatchArgs& args, int device, cudaStream_t s) {
   BatchArgs a = args;
   void* params[] = {&a};
   SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne_batch<NC, K>, dim3(grid),
-                                      dim3(kWarps * 32), params, 0, s));
+                                      dim3(kThreads), params, T::kSmem, s));
   sw_count_launch();
   return true;
 }
@@ -359,14 +538,19 @@ bool launch_b(const BatchArgs& args, int device, cudaStream_t s) {
 
 int cgne_batch_width(int nb) { return nb <= 4 ? 4 : (nb <= 8 ? 8 : 16); }
 
-bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, int nb, const double2* const* b,
-                       double2* const* x, double2* X, double2* R, double2* P, float2* Rf,
-                       float2* Pf, double* partials, unsigned* bar, int* status, int maxit,
-                       double tol, int device, cudaStream_t s) {
+void launch_adjoint_f32(const CoarseGeom& g, const double2* Y, float2* Yd, cudaStream_t s) {
+  k_adjoint_f32<<<g.E0 * g.E1 * 5, 256, 0, s>>>(Y, Yd, g.E0, g.E1, g.nc);
+  SW_LAUNCH_CHECK();
+}
+
+bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, int nb,
+                       const double2* const* b, double2* const* x, double2* X, double2* R,
+                       double2* P, float2* Rf, float2* Pf, double* partials, unsigned* bar,
+                       int* status, int maxit, double tol, int device, cudaStream_t s) {
   if (nb < 1 || nb > 16) return false;
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 18 * sizeof(int), s));
-  BatchArgs a{Yf, b, x, X, R, P, Rf, Pf, partials, bar, status, nb, g.E0, g.E1, maxit, tol};
+  BatchArgs a{Yf, Yd, b, x, X, R, P, Rf, Pf, partials, bar, status, nb, g.E0, g.E1, maxit, tol};
   int K = cgne_batch_width(nb);
 #define SW_CASE(NCV)                                   \
   case NCV:                                            \

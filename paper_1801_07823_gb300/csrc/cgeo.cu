@@ -158,6 +158,8 @@ extern "C" int sw_cg_eo_solve(sw_gauge* g, double mass, const void* b, void* x, 
   try {
     c->err.clear();
     SW_CUDA(cudaSetDevice(c->device));
+    cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) report_stale_error(stale);
     SW_REQUIRE(std::isfinite(mass) && mass > 0.0, SW_ERR_ARG, "mass must be > 0");
     SW_REQUIRE(tol > 0.0 && maxiter >= 0, SW_ERR_ARG, "tol must be > 0, maxiter >= 0");
     auto t0 = std::chrono::steady_clock::now();
@@ -181,10 +183,10 @@ extern "C" int sw_cg_eo_solve(sw_gauge* g, double mass, const void* b, void* x, 
         SW_CUDA(cudaMemcpyAsync(x, dx, N * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
       SW_CUDA(cudaStreamSynchronize(c->stream));
     } catch (...) {
-      cudaFree(work);
+      dev_free(work, "CG work");
       throw;
     }
-    cudaFree(work);
+    dev_free(work, "CG work");
     if (st) {
       std::memset(st, 0, sizeof(*st));
       st->converged = rc == SW_OK;

@@ -16,6 +16,7 @@
 //
 // Krylov coefficients stay on the device (Coef slots); the host reads back
 // only the residual norms its stopping tests branch on.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -43,8 +44,18 @@ double2* dalloc(long n) {
 }  // namespace
 
 void sw_mg_release(sw_mg* mg) {
-  for (double2* p : mg->allocs) cudaFree(p);
+  for (double2* p : mg->allocs) dev_free(p, "hierarchy buffer");
   mg->allocs.clear();
+}
+
+double2* ScopedBuffers::get(long n) {
+  double2* p = dalloc(n);
+  list.push_back(p);
+  return p;
+}
+
+ScopedBuffers::~ScopedBuffers() {
+  for (double2* p : list) dev_free(p, "call scratch");
 }
 
 double2* mg_alloc(sw_mg* mg, long n) {
@@ -52,19 +63,6 @@ double2* mg_alloc(sw_mg* mg, long n) {
   mg->allocs.push_back(p);
   return p;
 }
-
-// Setup-only buffers, released when the setup returns.
-struct TempBuffers {
-  std::vector<double2*> list;
-  double2* get(long n) {
-    double2* p = dalloc(n);
-    list.push_back(p);
-    return p;
-  }
-  ~TempBuffers() {
-    for (double2* p : list) cudaFree(p);
-  }
-};
 
 // ---------------------------------------------------------------- operators
 long level_len(const sw_mg* mg, int l) {
@@ -377,7 +375,7 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
     launch_to_f32(mg->binv, mg->binv32, N * 4, s);
     mg->s32tmp = (float2*)mg_alloc(mg, (N + 1) / 2);
   }
-  TempBuffers tmp;
+  ScopedBuffers tmp;
   for (int l = 0; l + 1 < mg->nlev; ++l) {
     MgLevel& L = mg->lev[l];
     MgLevel& C = mg->lev[l + 1];
@@ -792,9 +790,10 @@ void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
   SW_CUDA(cudaStreamSynchronize(c->stream));  // hp is a host stack array
   std::lock_guard<std::mutex> lock(g_persistent_mutex);
   int tk = timing_begin(c, kCatCgne);
-  bool ran = launch_cgne_batch(CoarseGeom{L.E0, L.E1, L.nc}, B.Yf, nb, B.dptr, B.dptr + 16, B.X,
-                               B.R, B.P, B.Rf, B.Pf, B.partials, B.bar, B.status,
-                               mg->p.coarsest_maxiter, mg->p.coarsest_tol, c->device, c->stream);
+  bool ran = launch_cgne_batch(CoarseGeom{L.E0, L.E1, L.nc}, B.Yf, B.Yd, nb, B.dptr,
+                               B.dptr + 16, B.X, B.R, B.P, B.Rf, B.Pf, B.partials, B.bar,
+                               B.status, mg->p.coarsest_maxiter, mg->p.coarsest_tol, c->device,
+                               c->stream);
   timing_end(c, tk);
   if (!ran)
     throw SwError{SW_ERR_ARG, "no batched coarsest solver for nc = " + std::to_string(L.nc)};
@@ -802,13 +801,17 @@ void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
   SW_CUDA(cudaMemcpyAsync(hst, B.status, sizeof(hst), cudaMemcpyDeviceToHost, c->stream));
   SW_CUDA(cudaStreamSynchronize(c->stream));
   if (!c->pending.empty()) timing_harvest(c);
-  if (hst[0]) throw SwError{SW_ERR_TIMEOUT, "batched coarsest CGNE: a grid barrier wait gave up"};
+  if (hst[0])
+    throw SwError{SW_ERR_TIMEOUT,
+                  "batched coarsest CGNE: a wait gave up or a buffer was misaligned"};
   if (hst[1]) throw SwError{SW_ERR_NAN, "non-finite norm in batched CGNE"};
+  int kernel_it = 0;  // the launch runs as many iterations as its slowest right-hand side
   for (int i = 0; i < nb; ++i) {
     bc.coarse_it[set[i]] += hst[2 + i];
     bc.coarse_solves[set[i]]++;
-    if (c->timing) c->t_count[kCatCgne + 1] += hst[2 + i];
+    kernel_it = std::max(kernel_it, hst[2 + i]);
   }
+  if (c->timing) c->t_count[kCatCgne + 1] += kernel_it;
 }
 
 void solve_level_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
@@ -875,6 +878,8 @@ void batch_alloc(sw_mg* mg) {
   long ysz = (long)C.E0 * C.E1 * 5 * C.nc * C.nc;
   B.Yf = (float2*)mg_alloc(mg, (ysz + 1) / 2);
   launch_to_f32(C.Y, B.Yf, ysz, mg->ctx->stream);
+  B.Yd = (float2*)mg_alloc(mg, (ysz + 1) / 2);
+  launch_adjoint_f32(CoarseGeom{C.E0, C.E1, C.nc}, C.Y, B.Yd, mg->ctx->stream);
   int sms = 0;
   SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mg->ctx->device));
   B.partials = (double*)mg_alloc(mg, (long)kMaxBatch * sms);  // 2 phases x 16 x SMs doubles

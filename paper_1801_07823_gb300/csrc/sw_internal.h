@@ -27,6 +27,12 @@ void sw_count_launch();
     sw_count_launch();            \
     SW_CUDA(cudaGetLastError());  \
   } while (0)
+// cudaFree that reports a failure on stderr (and clears it) instead of
+// leaving it pending for the next launch check.
+void dev_free(void* p, const char* what);
+// Notes on stderr (first few times) that an entry point cleared a pending
+// error of an earlier, unchecked runtime call of the process.
+void report_stale_error(cudaError_t e);
 #define SW_REQUIRE(cond, code, text)                 \
   do {                                               \
     if (!(cond)) throw SwError{(code), (text)};      \
@@ -220,14 +226,17 @@ bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const 
                             int device, cudaStream_t s, int stall_test = 0);
 
 // Batched coarsest CGNE (batch_cgne.cu): nb <= 16 right-hand sides, FP32
-// stencil Yf, FP64 iterates.  X, R, P: [n][K] double2, Rf, Pf: [n][K] float2,
+// forward stencil Yf and adjoint stencil Yd (launch_adjoint_f32), FP64
+// iterates.  X, R, P: [n][K] double2, Rf, Pf: [n][K] float2,
 // K = cgne_batch_width(nb); partials: 2 K SMs doubles; status: 18 ints
-// ([0] timeout, [1] non-finite, [2 + r] iterations).
+// ([0] wait timeout or misaligned buffer, [1] non-finite, [2 + r] iterations).
 int cgne_batch_width(int nb);
-bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, int nb, const double2* const* b,
-                       double2* const* x, double2* X, double2* R, double2* P, float2* Rf,
-                       float2* Pf, double* partials, unsigned* bar, int* status, int maxit,
-                       double tol, int device, cudaStream_t s);
+bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, int nb,
+                       const double2* const* b, double2* const* x, double2* X, double2* R,
+                       double2* P, float2* Rf, float2* Pf, double* partials, unsigned* bar,
+                       int* status, int maxit, double tol, int device, cudaStream_t s);
+// Yd[X][d] = Y[nb(X, d)][opp(d)]^dag in FP32, every block column-major like Y.
+void launch_adjoint_f32(const CoarseGeom& g, const double2* Y, float2* Yd, cudaStream_t s);
 
 // ------------------------------------------------------------- mixed.cu
 void fine_apply_S32(const sw_gauge* g, const float2* W32, const float2* binv32,

@@ -44,6 +44,7 @@ struct BatchWs {
   double2 *X = nullptr, *R = nullptr, *P = nullptr;  // coarsest CGNE, [n][K]
   float2 *Rf = nullptr, *Pf = nullptr;
   float2* Yf = nullptr;                  // FP32 copy of the coarsest stencil
+  float2* Yd = nullptr;                  // FP32 adjoint blocks of the coarsest stencil
   double* partials = nullptr;
   unsigned* bar = nullptr;
   int* status = nullptr;
@@ -78,6 +79,12 @@ struct sw_mg {
 inline int slot_base(int l) { return 64 * l; }
 
 double2* mg_alloc(sw_mg* mg, long n);
+// Device buffers owned by one library call, freed when it returns or throws.
+struct ScopedBuffers {
+  std::vector<double2*> list;
+  double2* get(long n);
+  ~ScopedBuffers();
+};
 void sw_mg_release(sw_mg* mg);
 void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed);
 int mg_coarsest_solve(sw_mg* mg, const double2* b, double2* x);  // CGNE on the coarsest level

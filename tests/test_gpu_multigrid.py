@@ -403,3 +403,41 @@ def test_batched_solves(sw, mixed64):
     for k in (0, 7, 15):
         assert sts[k]["converged"]
         assert np.linalg.norm(B16[k] - D @ X16[k]) / np.linalg.norm(B16[k]) <= 1e-10
+
+
+@pytest.mark.parametrize("L,blocks,nvec", [
+    (128, [(2, 2), (2, 2)], [8, 12]),  # 16x16 coarsest sites, nc 24: most CTAs own two sites
+    (64, [(2, 2), (2, 2)], [8, 32]),   # 8x8 coarsest sites, nc 64 (the widest stencil blocks)
+])
+def test_batched_coarsest_tiles(sw, ctx, L, blocks, nvec):
+    """Batched solves whose coarsest level has more sites than SMs, and one with
+    64 x 64 stencil blocks: every right-hand side reaches the 1e-10 true
+    residual (oracle D); a right-hand side gets the same solution in batches of
+    16, 7 and 1 at any position; outer iterations stay within 2 of its single
+    mixed solve."""
+    m = 0.01
+    th = si.heatbath_u1(L, L, 6.0, 300, seed=7, device="cuda")
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=params(sw, precision=sw.SW_MG_MIXED),
+                       psi0=psi0)
+    try:
+        D = operators.dirac(th, m)
+        B = np.stack([si.gaussian_complex(5000 + k, L * L) for k in range(16)])
+        X16 = np.zeros_like(B)
+        st16 = sw.sw_mg_solve_batch(h, B, X16, 1e-10)
+        for k in range(16):
+            r = np.linalg.norm(B[k] - D @ X16[k]) / np.linalg.norm(B[k])
+            assert st16[k]["converged"] and r <= 1e-10, (k, r)
+        X7 = np.zeros_like(B[:7])
+        sw.sw_mg_solve_batch(h, B[3:10], X7, 1e-10)
+        assert np.array_equal(X7[0], X16[3]) and np.array_equal(X7[6], X16[9])
+        X1 = np.zeros_like(B[:1])
+        sw.sw_mg_solve_batch(h, B[15:16], X1, 1e-10)
+        assert np.array_equal(X1[0], X16[15])
+        x = np.zeros(L * L, dtype=complex)
+        s1 = sw.sw_mg_solve(h, B[0], x, 1e-10)
+        assert abs(st16[0]["outer_iters"] - s1["outer_iters"]) <= 2
+    finally:
+        h.free()
+        g.free()
