@@ -26,8 +26,11 @@
 // CTAs in a fixed order with one CTA per SM for every K, so a right-hand side's
 // scalars, and hence its result, do not depend on its batch-mates.
 //
-// Layout inside the kernel: right-hand-side-minor, element (dof, rhs) at
-// dof * K + rhs, so a neighbour's nc x K vector block is contiguous.
+// Layout inside the kernel: right-hand-side-minor.  FP64 vectors hold element
+// (dof, rhs) at dof * K + rhs; the FP32 copies that feed the stencil are
+// planar per dof (K real parts, then K imaginary parts), so a neighbour's
+// nc x K block is contiguous and two right-hand sides' parts form the operand
+// pairs of one paired FP32 FMA (__ffma2_rn, each lane rounded like fmaf).
 #include <string>
 
 #include "sw_internal.h"
@@ -44,17 +47,22 @@ constexpr int kWarps = kThreads / 32;
 template <int NC, int K>
 struct Tile {
   static constexpr int kGroups = K / 4;              // four right-hand sides per thread
-  static constexpr int kTps = NC * kGroups;          // threads per site
+  // rows per thread: two when one row per thread would need the whole CTA for one site
+  static constexpr int kR = NC * kGroups > kThreads / 2 ? 2 : 1;
+  static constexpr int kRowsT = NC / kR;             // row slots per site
+  static constexpr int kTps = kRowsT * kGroups;      // threads per site
   static constexpr int kSiteF2 = NC * NC + NC * K;   // float2 per site and stage
   static constexpr int kSThr = kThreads / kTps;
-  static constexpr int kSMem0 = (72 * 1024) / (kSiteF2 * 8);
+  static constexpr int kSPair = kThreads / (4 * K);  // per-site norm tree: four threads per pair
+  static constexpr int kSMem0 = (100 * 1024) / (kSiteF2 * 8);
   static constexpr int kSMem = kSMem0 > 0 ? kSMem0 : 1;
-  static constexpr int kS = kSThr < kSMem ? kSThr : kSMem;
+  static constexpr int kS0 = kSThr < kSMem ? kSThr : kSMem;
+  static constexpr int kS = kS0 < kSPair ? kS0 : kSPair;
   static constexpr int kStageF2 = kS * kSiteF2;
   static constexpr int kStagesMem = (200 * 1024) / (kStageF2 * 8);
   static constexpr int kStages = kStagesMem < 4 ? kStagesMem : 4;
   static constexpr int kSmem = kStages * kStageF2 * 8;
-  static_assert(NC % 4 == 0 && K % 4 == 0, "rows and right-hand sides in fours");
+  static_assert(NC % 4 == 0 && K % 4 == 0 && NC % kR == 0, "rows and right-hand sides in fours");
   static_assert(kTps <= kThreads && kS >= 1 && kStages >= 2, "tile does not fit");
   static_assert(kS * K * 4 <= kThreads, "per-site norm tree needs four threads per pair");
 };
@@ -128,8 +136,8 @@ struct BatchArgs {
   double2* X;              // [n][K] FP64 iterates
   double2* R;              // [n][K] FP64 residuals
   double2* P;              // [n][K] FP64 directions
-  float2* Rf;              // [n][K] FP32 copies read by the stencil
-  float2* Pf;
+  float* Rf;               // [n][2][K] FP32 copies read by the stencil (planar per dof)
+  float* Pf;
   double* partials;        // [2][K][gridDim.x]
   unsigned* bar;           // grid barrier state (2 words)
   int* status;             // [0] wait timeout or misaligned buffer, [1] non-finite,
@@ -191,21 +199,36 @@ __device__ void cta_partials(const double* v, double (*red)[kWarps], double* par
 template <int K>
 __device__ void grid_sums(const double* part, double* out) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int G = gridDim.x;
   for (int r = w; r < K; r += kWarps) {
+    // all loads first, then the adds in the order of the lane-strided loop
+    const double* pr = part + r * G;
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = lane + 32 * k < G ? __ldcg(pr + lane + 32 * k) : 0.0;
     double s = 0.0;
-    for (int q = lane; q < (int)gridDim.x; q += 32) s += __ldcg(part + r * gridDim.x + q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (lane + 32 * k < G) s += v[k];
+    for (int q = lane + 256; q < G; q += 32) s += __ldcg(pr + q);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[r] = s;
   }
   __syncthreads();
 }
 
-// acc += y v for one complex product, FP32 (same operation order for every row).
-__device__ __forceinline__ void cmac(float2& acc, float2 y, float vx, float vy) {
-  acc.x = fmaf(y.x, vx, acc.x);
-  acc.x = fmaf(-y.y, vy, acc.x);
-  acc.y = fmaf(y.x, vy, acc.y);
-  acc.y = fmaf(y.y, vx, acc.y);
+// re += y v and im += y v for two right-hand sides at once: re and im hold the
+// real (imaginary) parts of the two sums, vr and vi the two right-hand sides'
+// real and imaginary parts.  Each lane runs fmaf(y.x, vx, .), fmaf(-y.y, vy, .)
+// for the real part and fmaf(y.x, vy, .), fmaf(y.y, vx, .) for the imaginary
+// part, the same sequence for every row and right-hand side.
+__device__ __forceinline__ void cmac2(float2& re, float2& im, float2 y, float2 vr, float2 vi) {
+  const float2 yx = make_float2(y.x, y.x), yy = make_float2(y.y, y.y);
+  const float2 nyy = make_float2(-y.y, -y.y);
+  re = __ffma2_rn(yx, vr, re);
+  re = __ffma2_rn(nyy, vi, re);
+  im = __ffma2_rn(yx, vi, im);
+  im = __ffma2_rn(yy, vr, im);
 }
 
 enum { kModeInit = 0, kModeXR = 1, kModeP = 2 };
@@ -235,9 +258,10 @@ template <int NC, int K, int MODE>
 __device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm,
                               unsigned& qbase) {
   using T = Tile<NC, K>;
+  constexpr int R = T::kR;
   const int t = threadIdx.x;
   const int s = t / T::kTps, w = t - s * T::kTps;
-  const int g = w % T::kGroups, i = w / T::kGroups;
+  const int g = w % T::kGroups, i = w / T::kGroups;  // rows i + k * kRowsT, k < R
   const bool act = s < T::kS;
   const int G = gridDim.x, cta = blockIdx.x;
   const int nsites = a.E0 * a.E1;
@@ -245,7 +269,7 @@ __device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm
   const int nchunks = (nmine + T::kS - 1) / T::kS;
   const int nst = nchunks * 5;
   const float2* Z = MODE == kModeXR ? a.Yf : a.Yd;
-  const float2* V = MODE == kModeXR ? a.Pf : a.Rf;
+  const float* V = MODE == kModeXR ? a.Pf : a.Rf;
 
   // stage q of this phase: chunk q / 5 of this CTA's sites, direction q % 5
   auto issue = [&](int q) {
@@ -259,7 +283,8 @@ __device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm
       const int Xs = cta + G * (c * T::kS + ss);
       const int nbs = nbr(Xs, d, a.E0, a.E1);
       bulk_load(buf + ss * NC * NC, Z + ((size_t)Xs * 5 + d) * NC * NC, NC * NC * 8, mb);
-      bulk_load(buf + T::kS * NC * NC + ss * NC * K, V + (size_t)nbs * NC * K, NC * K * 8, mb);
+      bulk_load(buf + T::kS * NC * NC + ss * NC * K, V + (size_t)nbs * NC * 2 * K, NC * K * 8,
+                mb);
     }
   };
 
@@ -273,9 +298,11 @@ __device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm
     const int m = c * T::kS + s;
     const bool valid = act && m < nmine;
     const int X = cta + G * m;
-    float2 acc[4];
+    // real / imaginary parts of the sums of right-hand sides (4g, 4g+1) and (4g+2, 4g+3)
+    float2 re01[R], re23[R], im01[R], im23[R];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int k = 0; k < R; ++k)
+      re01[k] = re23[k] = im01[k] = im23[k] = make_float2(0.f, 0.f);
     for (int d = 0; d < 5; ++d) {
       const int q = c * 5 + d;
       const unsigned Q = qbase + q;
@@ -286,16 +313,19 @@ __device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm
       }
       if (valid) {
         const float2* Ys = stage + (size_t)bi * T::kStageF2 + s * NC * NC + i;
-        const float2* Vs = stage + (size_t)bi * T::kStageF2 + T::kS * NC * NC + s * NC * K + 4 * g;
-#pragma unroll 8
+        const float* Vs = reinterpret_cast<const float*>(stage + (size_t)bi * T::kStageF2 +
+                                                         T::kS * NC * NC + s * NC * K) +
+                          4 * g;
+#pragma unroll 4
         for (int j = 0; j < NC; ++j) {
-          const float2 y = Ys[j * NC];
-          const float4 v01 = *reinterpret_cast<const float4*>(Vs + j * K);
-          const float4 v23 = *reinterpret_cast<const float4*>(Vs + j * K + 2);
-          cmac(acc[0], y, v01.x, v01.y);
-          cmac(acc[1], y, v01.z, v01.w);
-          cmac(acc[2], y, v23.x, v23.y);
-          cmac(acc[3], y, v23.z, v23.w);
+          const float4 vr = *reinterpret_cast<const float4*>(Vs + j * 2 * K);
+          const float4 vi = *reinterpret_cast<const float4*>(Vs + j * 2 * K + K);
+#pragma unroll
+          for (int k = 0; k < R; ++k) {
+            const float2 y = Ys[j * NC + k * T::kRowsT];
+            cmac2(re01[k], im01[k], y, make_float2(vr.x, vr.y), make_float2(vi.x, vi.y));
+            cmac2(re23[k], im23[k], y, make_float2(vr.z, vr.w), make_float2(vi.z, vi.w));
+          }
         }
       }
       __syncthreads();  // every thread is done with this buffer
@@ -304,46 +334,76 @@ __device__ void stencil_phase(const BatchArgs& a, float2* stage, Smem<NC, K>& sm
         issue(q + T::kStages);
       }
     }
-    double q2[4] = {0.0, 0.0, 0.0, 0.0};
-    if (valid) {
-      const size_t e = ((size_t)X * NC + i) * K + 4 * g;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = 4 * g + u;
+    for (int k = 0; k < R; ++k) {
+      const int row = i + k * T::kRowsT;
+      const float accx[4] = {re01[k].x, re01[k].y, re23[k].x, re23[k].y};
+      const float accy[4] = {im01[k].x, im01[k].y, im23[k].x, im23[k].y};
+      double q2[4] = {0.0, 0.0, 0.0, 0.0};
+      if (valid) {
+        const size_t e = ((size_t)X * NC + row) * K + 4 * g;          // FP64, interleaved
+        float* vf = (MODE == kModeXR ? a.Rf : a.Pf) + ((size_t)X * NC + row) * 2 * K + 4 * g;
+        float fr[4], fi[4];
         if (MODE == kModeInit) {
-          const double2 pv = make_double2((double)acc[u].x, (double)acc[u].y);
-          a.P[e + u] = pv;
-          a.Pf[e + u] = acc[u];
-          q2[u] = fma(pv.x, pv.x, pv.y * pv.y);
-        } else if (sm.state[r] == 0) {
-          if (MODE == kModeXR) {
-            const double al = sm.coef[r];
-            const double2 pv = __ldcg(a.P + e + u);
-            double2 xv = __ldcg(a.X + e + u), rv = __ldcg(a.R + e + u);
-            xv.x = fma(al, pv.x, xv.x);
-            xv.y = fma(al, pv.y, xv.y);
-            rv.x = fma(-al, (double)acc[u].x, rv.x);
-            rv.y = fma(-al, (double)acc[u].y, rv.y);
-            a.X[e + u] = xv;
-            a.R[e + u] = rv;
-            a.Rf[e + u] = make_float2((float)rv.x, (float)rv.y);
-            q2[u] = fma(rv.x, rv.x, rv.y * rv.y);
-          } else {
-            const double be = sm.coef[r];
-            double2 pv = __ldcg(a.P + e + u);
-            pv.x = fma(be, pv.x, (double)acc[u].x);
-            pv.y = fma(be, pv.y, (double)acc[u].y);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const double2 pv = make_double2((double)accx[u], (double)accy[u]);
             a.P[e + u] = pv;
-            a.Pf[e + u] = make_float2((float)pv.x, (float)pv.y);
+            fr[u] = accx[u];
+            fi[u] = accy[u];
             q2[u] = fma(pv.x, pv.x, pv.y * pv.y);
           }
-        }
-      }
-    }
-    // per-site sums over rows: four threads per (site, rhs) pair, NC/4 rows each
-    if (act) {
+        } else if (MODE == kModeXR) {
+          double2 pv[4], xv[4], rv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sm.sq[(s * K + 4 * g + u) * NC + i] = q2[u];
+          for (int u = 0; u < 4; ++u) {  // all loads first
+            pv[u] = __ldcg(a.P + e + u);
+            xv[u] = __ldcg(a.X + e + u);
+            rv[u] = __ldcg(a.R + e + u);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * g + u;
+            if (sm.state[r] == 0) {
+              const double al = sm.coef[r];
+              xv[u].x = fma(al, pv[u].x, xv[u].x);
+              xv[u].y = fma(al, pv[u].y, xv[u].y);
+              rv[u].x = fma(-al, (double)accx[u], rv[u].x);
+              rv[u].y = fma(-al, (double)accy[u], rv[u].y);
+              a.X[e + u] = xv[u];
+              a.R[e + u] = rv[u];
+              q2[u] = fma(rv[u].x, rv[u].x, rv[u].y * rv[u].y);
+            }
+            // a stopped right-hand side keeps r, so this rewrites the same FP32 value
+            fr[u] = (float)rv[u].x;
+            fi[u] = (float)rv[u].y;
+          }
+        } else {
+          double2 pv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pv[u] = __ldcg(a.P + e + u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * g + u;
+            if (sm.state[r] == 0) {
+              const double be = sm.coef[r];
+              pv[u].x = fma(be, pv[u].x, (double)accx[u]);
+              pv[u].y = fma(be, pv[u].y, (double)accy[u]);
+              a.P[e + u] = pv[u];
+              q2[u] = fma(pv[u].x, pv[u].x, pv[u].y * pv[u].y);
+            }
+            fr[u] = (float)pv[u].x;
+            fi[u] = (float)pv[u].y;
+          }
+        }
+        *reinterpret_cast<float4*>(vf) = make_float4(fr[0], fr[1], fr[2], fr[3]);
+        *reinterpret_cast<float4*>(vf + K) = make_float4(fi[0], fi[1], fi[2], fi[3]);
+      }
+      // per-site sums over rows: four threads per (site, rhs) pair, NC/4 rows each
+      if (act) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sm.sq[(s * K + 4 * g + u) * NC + row] = q2[u];
+      }
     }
     __syncthreads();
     {
@@ -416,7 +476,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_batch(BatchArgs a) {
       double2 v = r < a.nb ? a.b[r][dof] : make_double2(0.0, 0.0);
       a.X[e] = make_double2(0.0, 0.0);
       a.R[e] = v;
-      a.Rf[e] = make_float2((float)v.x, (float)v.y);
+      a.Rf[dof * 2 * K + r] = (float)v.x;
+      a.Rf[dof * 2 * K + K + r] = (float)v.y;
       nrm[r] = fma(v.x, v.x, fma(v.y, v.y, nrm[r]));
     }
   }
@@ -550,7 +611,8 @@ bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, 
   if (nb < 1 || nb > 16) return false;
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 18 * sizeof(int), s));
-  BatchArgs a{Yf, Yd, b, x, X, R, P, Rf, Pf, partials, bar, status, nb, g.E0, g.E1, maxit, tol};
+  BatchArgs a{Yf, Yd, b, x, X, R, P, reinterpret_cast<float*>(Rf), reinterpret_cast<float*>(Pf),
+              partials, bar, status, nb, g.E0, g.E1, maxit, tol};
   int K = cgne_batch_width(nb);
 #define SW_CASE(NCV)                                   \
   case NCV:                                            \

@@ -227,7 +227,8 @@ bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const 
 
 // Batched coarsest CGNE (batch_cgne.cu): nb <= 16 right-hand sides, FP32
 // forward stencil Yf and adjoint stencil Yd (launch_adjoint_f32), FP64
-// iterates.  X, R, P: [n][K] double2, Rf, Pf: [n][K] float2,
+// iterates.  X, R, P: [n][K] double2; Rf, Pf: n K float2 of scratch (the
+// kernel keeps them planar per dof: K real parts, then K imaginary parts),
 // K = cgne_batch_width(nb); partials: 2 K SMs doubles; status: 18 ints
 // ([0] wait timeout or misaligned buffer, [1] non-finite, [2 + r] iterations).
 int cgne_batch_width(int nb);
