@@ -21,7 +21,12 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# The oracle timings (cpu_baseline, --impl reference) are single-core: keep
+# BLAS from spawning threads before numpy loads it.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -62,6 +67,26 @@ def _profiled_traffic(profile: str, source: str, key: str):
     if sha is None or sha.strip() != want or key not in fields:
         return None
     return float(fields[key])
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks, on every rank (x itself on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rhs_seed(rank: int, k: int, offset: int = 0) -> int:
+    """Seed of right-hand side k of a rank: replicas solve different systems."""
+    return rank * 1000 + offset + k
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 def parse():
@@ -334,7 +359,7 @@ def run_native(args, rank, world, local):
     setup_s = time.perf_counter() - t
 
     nsteps = args.warmup + args.steps
-    B = [torch.from_numpy(rhs(rank * 1000 + k, L)).cuda() for k in range(nsteps)]
+    B = [torch.from_numpy(rhs(rhs_seed(rank, k), L)).cuda() for k in range(nsteps)]
     X = torch.zeros_like(B[0])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
@@ -365,11 +390,8 @@ def run_native(args, rank, world, local):
     sw.sw_set_timing(ctx, False)
     clocks = clk.summary()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    value = world * args.steps / elapsed
+    elapsed = max_over_ranks(elapsed, world)
+    value = job_rate(world, args.steps, elapsed)
     ok = all(s["converged"] and s["true_resid"] <= WORKLOAD["tol"] for s in timed)
 
     # end to end through the C ABI with pinned host buffers (copies inside the call)
@@ -381,14 +403,11 @@ def run_native(args, rank, world, local):
     barrier()
     t0 = time.perf_counter()
     for k in range(args.warmup, nsteps):
-        hb.numpy()[:] = rhs(rank * 1000 + k, L)
+        hb.numpy()[:] = rhs(rhs_seed(rank, k), L)
         sw.sw_mg_solve(h, hb.numpy(), hx.numpy(), WORKLOAD["tol"])
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, world)
 
     # roofline of the dominant kernel (FP64 complex MAC = 8 flop; FP64-ALU bound on GB300):
     # the persistent coarsest CGNE (category 5: 2 stencil applications per iteration)
@@ -455,13 +474,10 @@ def run_native(args, rank, world, local):
         e1_.record(stream)
         barrier()
         mel = e0_.elapsed_time(e1_) / 1e3
-        if world > 1:
-            tt = torch.tensor([mel], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            mel = float(tt.item())
+        mel = max_over_ranks(mel, world)
         m0 = mt[0]
         variants["mixed"] = {
-            "value": world * args.steps / mel, "unit": UNIT, "ms_per_step": mel / args.steps * 1e3,
+            "value": job_rate(world, args.steps, mel), "unit": UNIT, "ms_per_step": mel / args.steps * 1e3,
             "dtype": "f64 outer FGCR and vectors; f32 fine smoother; f16 (scaled) level-2 "
                      "stencil; double-float coarsest stencil",
             "converged_all": all(x_["converged"] and x_["true_resid"] <= WORKLOAD["tol"] for x_ in mt),
@@ -469,11 +485,11 @@ def run_native(args, rank, world, local):
             "outer_iters": m0["outer_iters"],
             "inter_avg": m0["inter_iters"] / max(m0["inter_solves"], 1),
             "coarsest_avg": m0["coarsest_iters"] / max(m0["coarsest_solves"], 1),
-            "speedup_vs_fp64": (world * args.steps / mel) / value}
+            "speedup_vs_fp64": job_rate(world, args.steps, mel) / value}
         # batched: 16 right-hand sides per sw_mg_solve_batch call on the same mixed
         # hierarchy (lockstep K-cycle, one batched FP32 coarsest CGNE per level visit)
         nbat = 16
-        BB = torch.stack([torch.from_numpy(rhs(rank * 1000 + 500 + k, L)) for k in range(nbat)]).cuda()
+        BB = torch.stack([torch.from_numpy(rhs(rhs_seed(rank, k, 500), L)) for k in range(nbat)]).cuda()
         XB = torch.zeros_like(BB)
         sw.sw_mg_solve_batch(hm, BB, XB, WORKLOAD["tol"])  # warm-up (allocates the workspace)
         barrier()
@@ -486,12 +502,9 @@ def run_native(args, rank, world, local):
         bel = e0_.elapsed_time(e1_) / 1e3
         bk = sw.sw_kernel_times(ctx, 7)
         sw.sw_set_timing(ctx, False)
-        if world > 1:
-            tt = torch.tensor([bel], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            bel = float(tt.item())
+        bel = max_over_ranks(bel, world)
         variants["batched16_mixed"] = {
-            "value": world * nbat / bel, "unit": UNIT, "ms_per_batch": bel * 1e3,
+            "value": job_rate(world, nbat, bel), "unit": UNIT, "ms_per_batch": bel * 1e3,
             "dtype": "f64 outer FGCR and vectors; f32 fine smoother; f16 (scaled) level-2 "
                      "stencil; f32 batched coarsest stencil",
             "converged_all": all(x_["converged"] and x_["true_resid"] <= WORKLOAD["tol"] for x_ in bt),
@@ -503,7 +516,7 @@ def run_native(args, rank, world, local):
                                 "iterations": bk[6][0],
                                 "us_per_iteration": 1e3 * bk[5][1] / max(bk[6][0], 1),
                                 "share": bk[5][1] / (bel * 1e3)},
-            "speedup_vs_fp64": (world * nbat / bel) / value}
+            "speedup_vs_fp64": job_rate(world, nbat, bel) / value}
         hm.free()
         # the paper's comparison solver on the same system: CG on the even/odd
         # normal equations (Sec. II, Fig. iterworst), FP64
@@ -514,9 +527,9 @@ def run_native(args, rank, world, local):
         ct = [sw.sw_cg_eo_solve(g, m, B[k], X, WORKLOAD["tol"]) for k in range(args.warmup, nsteps)]
         e1_.record(stream)
         barrier()
-        cel = e0_.elapsed_time(e1_) / 1e3
+        cel = max_over_ranks(e0_.elapsed_time(e1_) / 1e3, world)
         variants["cg_eo"] = {
-            "value": world * args.steps / cel, "unit": UNIT, "ms_per_step": cel / args.steps * 1e3,
+            "value": job_rate(world, args.steps, cel), "unit": UNIT, "ms_per_step": cel / args.steps * 1e3,
             "dtype": "f64", "iterations": ct[0]["outer_iters"],
             "converged_all": all(x_["converged"] for x_ in ct),
             "true_resid_max": max(x_["true_resid"] for x_ in ct),
@@ -551,7 +564,7 @@ def run_native(args, rank, world, local):
             "config": dict(WORKLOAD, L=L, sweeps=args.sweeps, parallelism=f"replicas x{world}",
                            l2="flushed between solves (256 MiB write)"),
             "clocks": clocks,
-            "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": job_rate(world, args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": 16 * L * L, "d2h_bytes_per_step": 16 * L * L},
             "gpu_launches": int(launches),
             "roofline": roof,
