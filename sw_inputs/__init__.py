@@ -206,6 +206,22 @@ def heatbath_u1(L0: int, L1: int, beta: float, sweeps: int, seed: int,
     return th.cpu().numpy()
 
 
+def null_vector_guesses(L0: int, L1: int, nvec, levels: int, blocks, seed: int = 5):
+    """Initial guesses of the null vectors, one [nvec[l], ndof] array per
+    level l = 0 .. levels-2: Gaussian vectors from streams stream_seed(seed, l, i).
+    Level 0 has one dof per fine site; level 1 has 2 nvec[0] dof per aggregate
+    of blocks[0] KD blocks (2 blocks[0] fine sites per direction), and each
+    further level 2 nvec[l-1] dof per aggregate of blocks[l-1] sites."""
+    out = [np.stack([gaussian_complex(stream_seed(seed, 0, i), L0 * L1) for i in range(nvec[0])])]
+    E0, E1 = L0 // (2 * blocks[0][0]), L1 // (2 * blocks[0][1])
+    nc = 2 * nvec[0]
+    for lv in range(1, levels - 1):
+        out.append(np.stack([gaussian_complex(stream_seed(seed, lv, i), E0 * E1 * nc)
+                             for i in range(nvec[lv])]))
+        E0, E1, nc = E0 // blocks[lv][0], E1 // blocks[lv][1], 2 * nvec[lv]
+    return out
+
+
 def plaquette_mean(theta: np.ndarray) -> float:
     """Average cos(theta_p) over all plaquettes (input-quality diagnostic)."""
     t0, t1 = theta[0], theta[1]

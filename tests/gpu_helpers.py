@@ -10,15 +10,7 @@ def relerr(a, b):
 
 def psi0_arrays(L0, L1, nvec, levels, blocks, seed=5):
     """Initial null-vector guesses per level, vector-major numpy arrays."""
-    out = [np.stack([si.gaussian_complex(si.stream_seed(seed, 0, i), L0 * L1)
-                     for i in range(nvec[0])])]
-    E0, E1 = L0 // (2 * blocks[0][0]), L1 // (2 * blocks[0][1])
-    nc = 2 * nvec[0]
-    for l in range(1, levels - 1):
-        out.append(np.stack([si.gaussian_complex(si.stream_seed(seed, l, i), E0 * E1 * nc)
-                             for i in range(nvec[l])]))
-        E0, E1, nc = E0 // blocks[l][0], E1 // blocks[l][1], 2 * nvec[l]
-    return out
+    return si.null_vector_guesses(L0, L1, nvec, levels, blocks, seed)
 
 
 def compact_P(Psp, chir, agg, nv):
