@@ -23,7 +23,7 @@ import time
 
 # The oracle timings (cpu_baseline, --impl reference) are single-core: keep
 # BLAS from spawning threads before numpy loads it.
-for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
@@ -179,27 +179,47 @@ def rhs(seed, L):
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def oracle_apply_times(th, m, psi0, reps=5):
-    """Per-application time of the oracle's S, A_hat (level 2) and A_hat (level 3)
-    on the workload's hierarchy built with zero setup CG steps (same shapes and
-    sparsity as the real hierarchy)."""
+COUNTS_FILE = os.path.join(ROOT, "oracle", "solve_counts_256.json")
+
+
+def oracle_counts(L):
+    """Application counts and wall-time ratio of the oracle's own full solve of
+    this workload (written by oracle/solve_counts.py), or None for another size."""
+    try:
+        with open(COUNTS_FILE) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    return rec if rec["workload"]["L"] == L else None
+
+
+def oracle_hierarchy(th, m, psi0):
+    """The oracle's hierarchy of this workload built with zero setup CG steps:
+    the shapes and sparsity of the real one, for timing its operators."""
     from oracle import mg as omg
-    H = omg.Hierarchy(th, m, 3, [tuple(b) for b in WORKLOAD["blocks"]], WORKLOAD["nvec"],
-                      [list(a) for a in psi0], omg.Params(setup_maxiter=0))
-    out = {}
-    ve = np.ones(H.F.even.size, dtype=complex)
-    t = time.perf_counter()
-    for _ in range(reps):
-        H.F.schur(ve)
-    out["S"] = (time.perf_counter() - t) / reps
-    for l in (1, 2):
-        op = H.levels[l].op
-        v = np.ones(op.shape[0], dtype=complex)
-        t = time.perf_counter()
-        for _ in range(reps):
-            op @ v
-        out[f"A{l + 1}"] = (time.perf_counter() - t) / reps
-    return out
+    return omg.Hierarchy(th, m, 3, [tuple(b) for b in WORKLOAD["blocks"]], WORKLOAD["nvec"],
+                         [list(a) for a in psi0], omg.Params(setup_maxiter=0))
+
+
+def oracle_solve_seconds(H, rec, reps):
+    """Seconds per oracle solve from a bounded sample: `reps` applications each of
+    the oracle's S, A_hat (level 2) and A_hat (level 3) timed here, weighted by
+    the counts of the oracle's own full solve and scaled by that solve's ratio of
+    wall time to application time.  Returns (seconds, per-application times)."""
+    from oracle.solve_counts import apply_times
+    ta = apply_times(H, reps)
+    c = rec["counts"]
+    return rec["overhead_ratio"] * sum(c[k] * ta[k] for k in c), ta
+
+
+def oracle_sample_note(rec, ta, reps):
+    c = rec["counts"]
+    return (f"{reps} applications each of the oracle's S, A_hat2, A_hat3 timed here "
+            f"({ta['S'] * 1e3:.2f}, {ta['A2'] * 1e3:.2f}, {ta['A3'] * 1e3:.2f} ms), weighted by "
+            f"the application counts of the oracle's own full solve of this workload "
+            f"({c['S']}, {c['A2']}, {c['A3']}) and scaled by its wall/application-time ratio "
+            f"{rec['overhead_ratio']:.3f} (oracle/solve_counts_256.json, measured once on "
+            f"{rec['machine']['processor']}); extrapolated")
 
 
 def dslash_bandwidth(sw, ctx, L=4096, reps=20):
@@ -279,61 +299,42 @@ def serving_measurement(nreq, seed=11):
 
 
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle on the same workload: a bounded run (one outer FGCR
-    iteration per step, hierarchy from a setup with 20 CG steps per null vector)
-    whose residual reduction gives the number of outer iterations to 1e-10."""
+    """The FP64 CPU oracle on the same workload, timed in bounded samples: every
+    step times applications of the oracle's operators on this machine, and a
+    solve's time is extrapolated from them with the application counts of the
+    oracle's own full solve of the workload (oracle_solve_seconds)."""
     if rank != 0:
         return
-    from oracle import mg as omg
     L = args.L
+    rec = oracle_counts(L)
+    if rec is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle solve counts for "
+                          f"L = {L} (oracle/solve_counts.py records the 256^2 workload)"}),
+              flush=True)
+        return
     dev = "cpu"
     try:
         import torch
         if torch.cuda.is_available():
-            dev = "cuda"  # input generation only; the solve below is the CPU oracle
+            dev = "cuda"  # input generation only; everything timed below is the CPU oracle
     except ImportError:
         pass
     th, psi0 = gauge_and_psi0(L, WORKLOAD["beta"], args.sweeps, dev)
-    m = WORKLOAD["mass"]
-    H = omg.Hierarchy(th, m, 3, [tuple(b) for b in WORKLOAD["blocks"]], WORKLOAD["nvec"],
-                      [list(a) for a in psi0], omg.Params(setup_maxiter=20, coarsest_maxiter=2048))
-    times, rates = [], []
-
+    H = oracle_hierarchy(th, WORKLOAD["mass"], psi0)
+    reps = 40
+    times = []
     for k in range(args.warmup + args.steps):
-        b = rhs(k, L)
-        hist = []
-
-        def on_iter(it, r):
-            hist.append(np.linalg.norm(r))
-            if it >= 1:
-                raise StopIteration
-
-        t = time.perf_counter()
-        try:
-            H.solve(b, WORKLOAD["tol"], on_outer=on_iter)
-        except StopIteration:
-            pass
-        dt = time.perf_counter() - t
-        bt = np.linalg.norm(H.F.schur_rhs(b))
-        rho = hist[-1] / bt
+        t_solve, ta = oracle_solve_seconds(H, rec, reps)
         if k >= args.warmup:
-            times.append(dt)
-            rates.append(rho)
-    rho = float(np.exp(np.mean(np.log(rates))))
-    n_outer = math.ceil(math.log(WORKLOAD["tol"]) / math.log(rho))
-    t_solve = float(np.mean(times)) * n_outer
+            times.append(t_solve)
+    t_solve = float(np.mean(times))
     value = 1.0 / t_solve
-    cores = 1
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(WORKLOAD, L=L, sweeps=args.sweeps),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"one outer FGCR iteration per step of the numpy/scipy "
-                                       f"oracle (setup capped at 20 CG steps per null vector); "
-                                       f"outer iterations to 1e-10 extrapolated from the "
-                                       f"measured residual reduction {rho:.3g} per iteration "
-                                       f"-> {n_outer}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": oracle_sample_note(rec, ta, reps)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -544,17 +545,16 @@ def run_native(args, rank, world, local):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            ta = oracle_apply_times(th, m, psi0)
-            nS = np.mean([s["fine_applies"] for s in timed])
-            n2 = ktimes[1][0] / args.steps
-            n3 = (ktimes[2][0] + 2 * ktimes[6][0]) / args.steps
-            t_cpu = nS * ta["S"] + n2 * ta["A2"] + n3 * ta["A3"]
+            rec = oracle_counts(L)
+            if rec is None:  # no full-solve record for this size: the GPU solves' counts
+                rec = {"counts": {"S": float(np.mean([s["fine_applies"] for s in timed])),
+                                  "A2": ktimes[1][0] / args.steps,
+                                  "A3": (ktimes[2][0] + 2 * ktimes[6][0]) / args.steps},
+                       "overhead_ratio": 1.0, "machine": {"processor": "(GPU solve counts, "
+                                                                       "BLAS-1 excluded)"}}
+            t_cpu, ta = oracle_solve_seconds(oracle_hierarchy(th, m, psi0), rec, reps=5)
             cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"oracle sparse applications timed on this workload's hierarchy "
-                             f"(S {ta['S'] * 1e3:.2f} ms, A_hat2 {ta['A2'] * 1e3:.2f} ms, A_hat3 "
-                             f"{ta['A3'] * 1e3:.2f} ms, 5 reps each), times the per-solve "
-                             f"application counts of the GPU solves ({nS:.0f}, {n2:.0f}, "
-                             f"{n3:.0f}); Krylov BLAS-1 excluded (extrapolated)"}
+                   "sample": oracle_sample_note(rec, ta, 5)}
         s0 = timed[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
