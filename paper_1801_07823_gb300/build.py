@@ -2,7 +2,7 @@
 
 Each translation unit compiles in its own nvcc process (in parallel), then
 nvcc links the shared library.  The CUDA runtime is linked statically, so the
-library needs only the driver at run time.
+library needs only the CUDA driver library (libcuda) at run time.
 """
 from __future__ import annotations
 

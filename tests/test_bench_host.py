@@ -30,7 +30,7 @@ def test_stored_counts_describe_the_workload():
     assert c["S"] == rec["stats"]["fine_applies"]
     # every coarsest CGNE iteration applies A_hat and its adjoint once
     assert c["A3"] >= 2 * rec["stats"]["coarsest_iters"]
-    # wall time over the time of the counted applications alone (timing noise around 1:
+    # wall time over the time of the counted applications alone (near 1 up to timing noise:
     # the coarsest applications dominate the oracle's solve)
     assert 0.8 <= rec["overhead_ratio"] <= 2.0
     assert bench.oracle_counts(bench.WORKLOAD["L"] // 2) is None

@@ -157,7 +157,7 @@ def load_localblock():
 def test_local_block_matches_paper(seed):
     """Eq. localblock.  The printed block equals eps B eps of Eq. staggeredD's B
     (the printed hopping has the opposite sign of Eq. staggeredD; eps B eps =
-    2m - B flips exactly the hops) -- the sign reading recorded in the design doc."""
+    2m - B flips exactly the hops): Eq. staggeredD's sign is the normative one."""
     L, m = 8, 0.23
     th = rand_theta(L, seed)
     U = operators.links(th)
