@@ -567,6 +567,8 @@ def run_native(args, rank, world, local):
             "e2e": {"value": job_rate(world, args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": 16 * L * L, "d2h_bytes_per_step": 16 * L * L},
             "gpu_launches": int(launches),
+            # ncu window over the timed solves: -k regex:^k_ -s <this> -c <gpu_launches>
+            "launches_before_timed": int(launches0),
             "roofline": roof,
             "cpu_baseline": cpu,
             "solve": {"converged_all": ok, "true_resid_max": max(s["true_resid"] for s in timed),
