@@ -148,8 +148,11 @@ int sw_dslash(sw_gauge* g, double mass, int op, int precision, const void* in, v
 /* Multigrid setup (Sec. IV): near-null vectors from CG on A A^dag, global
  * orthonormalisation, chiral doubling with (1 +- eps)/2 (level 1) or
  * (1 +- sigma3)/2 (coarser), block orthonormalisation, Galerkin coarse
- * operator P^dag A P, recursively.  All FP64.
- *  levels    2 or 3.
+ * operator P^dag A P, recursively.  The setup runs in FP64; with
+ * params->precision = SW_MG_MIXED it also keeps the reduced-precision copies
+ * of the operators that the mixed solve uses.
+ *  levels    2, 3 or 4 (Sec. IV: the recursion applies to every coarser
+ *            level).
  *  block     [levels-1][2] aggregate extents: block[0] in KD blocks (even
  *            values; 4,4 in the paper), block[l>0] in coarse sites (2,2).
  *  nvec      [levels-1] null vectors per level (8, 12 in the paper).
