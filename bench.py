@@ -539,7 +539,10 @@ def run_native(args, rank, world, local):
     dslash = None if args.no_variants else dslash_bandwidth(sw, ctx)
     serving = None
     if args.serving_requests > 0 and rank == 0:
-        serving = serving_measurement(args.serving_requests)
+        try:  # a failure here must not cost the headline line
+            serving = serving_measurement(args.serving_requests)
+        except Exception as exc:
+            serving = {"error": f"{type(exc).__name__}: {exc}"}
 
     line = None
     if rank == 0:

@@ -14,6 +14,15 @@ same whether it runs alone or in the mix.
 
 Masses are served from a fixed grid (hierarchies are per mass): a request's
 mass is rounded to the nearest grid value on a log scale.
+
+With batch_max > 1 a worker that takes a request also takes the other queued
+requests on the same hierarchy (same gauge field and mass, hence the same
+level shapes), up to batch_max in all, and solves them in one
+sw_mg_solve_batch call (on a mixed hierarchy: one lockstep K-cycle and one
+batched coarsest solve per visit).  Every request then goes through
+sw_mg_solve_batch, whose result for a right-hand side does not depend on its
+batch-mates, so a request's result is still the same whatever it was grouped
+with.  The admission model then also counts the batch workspace.
 """
 from __future__ import annotations
 
@@ -25,7 +34,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import SW_MG_MIXED, sw_context_create, sw_gauge_load, sw_mg_params_default, sw_mg_setup
-from . import sw_mg_solve
+from . import sw_mg_solve, sw_mg_solve_batch
 
 
 def hierarchy_bytes(L: int, blocks, nvec, mixed: bool, outer_restart: int = 32,
@@ -54,6 +63,31 @@ def hierarchy_bytes(L: int, blocks, nvec, mixed: bool, outer_restart: int = 32,
     return int(b)
 
 
+def batch_workspace_bytes(L: int, blocks, nvec, outer_restart: int = 32,
+                          inter_restart: int = 8, width: int = 16) -> int:
+    """Device bytes of the workspace of batched solves (allocated on the first
+    one, for `width` right-hand sides), from the sizes of its arrays."""
+    N = L * L
+    lens = [N // 2]                                 # level 1: even half of the fine lattice
+    E, nc = L, 1
+    for l, (blk, nv) in enumerate(zip(blocks, nvec)):
+        E = E // (2 * blk[0]) if l == 0 else E // blk[0]
+        nc = 2 * nv
+        lens.append(E * E * nc)
+    b = 0
+    for l, n in enumerate(lens):
+        last = l == len(lens) - 1
+        nbas = 0 if last else (outer_restart if l == 0 else inter_restart)
+        per_rhs = 2 if last else 2 + 2 + 2 * nbas + 6
+        b += width * per_rhs * n * 16
+    nc_last = lens[-1]
+    sites = nc_last // nc
+    b += 3 * nc_last * width * 16 + 2 * nc_last * width * 8    # iterates, FP32 stencil inputs
+    b += 2 * sites * 5 * nc * nc * 8                          # FP32 stencil and adjoint blocks
+    b += 3 * N * width * 16                                   # fine staging buffers
+    return int(b)
+
+
 @dataclass(order=True)
 class Request:
     arrival: float
@@ -66,6 +100,7 @@ class Request:
     finish: float = field(default=0.0, compare=False)
     worker: int = field(default=-1, compare=False)
     stats: dict = field(default=None, compare=False)
+    batch: int = field(default=1, compare=False)     # requests solved in the same call
 
 
 class Server:
@@ -76,7 +111,8 @@ class Server:
     hierarchies may use in total."""
 
     def __init__(self, gauges, masses, workers=2, hbm_budget=40 << 30, tol=1e-10, mixed=True,
-                 blocks=((4, 4), (2, 2)), nvec=(24, 32), params=None, device=0, psi0_fn=None):
+                 blocks=((4, 4), (2, 2)), nvec=(24, 32), params=None, device=0, psi0_fn=None,
+                 batch_max=1):
         import torch
         self.torch = torch
         self.gauges = gauges
@@ -88,6 +124,7 @@ class Server:
         self.params = params or {}
         self.budget = hbm_budget
         self.psi0_fn = psi0_fn
+        self.batch_max = max(1, min(16, int(batch_max)))
         self.lock = threading.Condition()
         self.queue: list[Request] = []
         self.done: list[Request] = []
@@ -138,7 +175,18 @@ class Server:
     # ------------------------------------------------------------------ workers
     def _footprint(self, gauge: int) -> int:
         L = self.gauges[gauge][0].shape[-1]
-        return hierarchy_bytes(L, self.blocks, self.nvec, self.mixed)
+        b = hierarchy_bytes(L, self.blocks, self.nvec, self.mixed)
+        if self.batch_max > 1 and self.mixed:
+            b += batch_workspace_bytes(L, self.blocks, self.nvec)
+        return b
+
+    def _companions(self, r):
+        """Queued requests on r's hierarchy, earliest first, that join r's batch
+        (lock held)."""
+        if self.batch_max <= 1:
+            return []
+        same = sorted(q for q in self.queue if q is not r and (q.gauge, q.mass) == (r.gauge, r.mass))
+        return same[:self.batch_max - 1]
 
     def _pick(self, wk):
         """Request this worker serves next (lock held): the earliest one whose
@@ -168,14 +216,18 @@ class Server:
                         return
                     r, need = self._pick(wk) if self.queue else (None, 0)
                     if r is not None:
-                        self.queue = [q for q in self.queue if q is not r]
+                        batch = [r] + self._companions(r)
+                        taken = {id(q) for q in batch}
+                        self.queue = [q for q in self.queue if id(q) not in taken]
                         heapq.heapify(self.queue)
                         self.used += need
                         wk["busy"] = True
                         break
                     self.lock.wait(timeout=0.05)
-            r.start = time.perf_counter()
-            r.worker = wk["id"]
+            t_start = time.perf_counter()
+            for q in batch:
+                q.start = t_start
+                q.worker = wk["id"]
             try:
                 with torch.cuda.stream(wk["stream"]):
                     key = (r.gauge, r.mass)
@@ -197,15 +249,26 @@ class Server:
                         wk["cache"][key] = dict(mg=mg, bytes=need, last=0.0)
                     h = wk["cache"][key]
                     h["last"] = time.perf_counter()
-                    x = np.zeros_like(r.b)
-                    r.stats = sw_mg_solve(h["mg"], r.b, x, self.tol, allow_noconv=True)
-                    r.x = x
-            except Exception as exc:  # a failed request is reported, the worker goes on
-                r.stats = {"converged": 0, "error": f"{type(exc).__name__}: {exc}"}
-            r.finish = time.perf_counter()
+                    if self.batch_max > 1:
+                        B = np.stack([q.b for q in batch])
+                        X = np.zeros_like(B)
+                        sts = sw_mg_solve_batch(h["mg"], B, X, self.tol, allow_noconv=True)
+                        for q, xq, sq in zip(batch, X, sts):
+                            q.x, q.stats = xq, sq
+                    else:
+                        x = np.zeros_like(r.b)
+                        r.stats = sw_mg_solve(h["mg"], r.b, x, self.tol, allow_noconv=True)
+                        r.x = x
+            except Exception as exc:  # failed requests are reported, the worker goes on
+                for q in batch:
+                    q.stats = {"converged": 0, "error": f"{type(exc).__name__}: {exc}"}
+            t_end = time.perf_counter()
+            for q in batch:
+                q.finish = t_end
+                q.batch = len(batch)
             with self.lock:
                 wk["busy"] = False
-                self.done.append(r)
+                self.done.extend(batch)
                 self.lock.notify_all()
 
 
@@ -218,7 +281,8 @@ def latency_summary(done) -> dict:
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
             "solves_per_s": float(lat.size / span), "makespan_s": float(span),
             "all_converged": bool(all(r.stats.get("converged") for r in done)),
-            "failed": int(sum(1 for r in done if not r.stats.get("converged")))}
+            "failed": int(sum(1 for r in done if not r.stats.get("converged"))),
+            "mean_batch": float(np.mean([r.batch for r in done]))}
 
 
 def poisson_stream(server, requests, rate, seed=0):

@@ -1,9 +1,10 @@
 """Host logic of the serving loop on CPU, with the library calls and CUDA
 streams replaced by fakes: admission under the HBM budget with LRU eviction,
-reuse of resident hierarchies, mass snapping, failure isolation and the
-latency summary."""
+reuse of resident hierarchies, mass snapping, failure isolation, batching of
+requests on one hierarchy and the latency summary."""
 import contextlib
 import threading
+import time
 import types
 
 import numpy as np
@@ -19,6 +20,8 @@ class _Fake:
         self.max_live = 0
         self.setups = 0
         self.fail_mass = None  # a setup at this mass raises
+        self.setup_delay = 0.0
+        self.batches = []      # (mass, request ids) per batched call
 
     def context_create(self, device, stream):
         return types.SimpleNamespace(free=lambda: None)
@@ -32,6 +35,7 @@ class _Fake:
     def mg_setup(self, g, mass, levels, blocks, nvec, params=None, psi0=None):
         if mass == self.fail_mass:
             raise RuntimeError("setup failed")
+        time.sleep(self.setup_delay)
         fake = self
 
         class _MG:
@@ -56,6 +60,14 @@ class _Fake:
         x[:] = b / mg.mass
         return {"converged": 1, "outer_iters": 1, "true_resid": 0.0}
 
+    def mg_solve_batch(self, mg, B, X, tol, allow_noconv=False):
+        assert not mg.freed and B.ndim == 2 and X.shape == B.shape
+        with self.lock:
+            self.batches.append((mg.mass, B[:, 0].real.astype(int).tolist()))
+        time.sleep(0.02)
+        X[:] = B / mg.mass
+        return [{"converged": 1, "outer_iters": 1, "true_resid": 0.0} for _ in range(len(B))]
+
 
 @pytest.fixture()
 def fake(monkeypatch):
@@ -65,6 +77,7 @@ def fake(monkeypatch):
     monkeypatch.setattr(serve, "sw_mg_params_default", f.params_default)
     monkeypatch.setattr(serve, "sw_mg_setup", f.mg_setup)
     monkeypatch.setattr(serve, "sw_mg_solve", f.mg_solve)
+    monkeypatch.setattr(serve, "sw_mg_solve_batch", f.mg_solve_batch)
     import torch
     monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: types.SimpleNamespace(cuda_stream=0))
     monkeypatch.setattr(torch.cuda, "device", lambda *a, **k: contextlib.nullcontext())
@@ -134,5 +147,33 @@ def test_failed_setup_is_reported_and_worker_goes_on(fake):
         s = serve.latency_summary(srv.done)
         assert s["requests"] == 2 and s["failed"] == 1 and not s["all_converged"]
         assert 0 <= s["p50_s"] <= s["p99_s"]
+    finally:
+        srv.close()
+
+
+def test_requests_on_one_hierarchy_are_batched(fake):
+    """batch_max > 1: requests queued on the same (gauge, mass) share one
+    batched call, never with another hierarchy's; results and accounting per
+    request are unchanged."""
+    fake.setup_delay = 0.2          # the first setup lets the queue fill
+    gauges = _gauges(n=2)
+    srv = serve.Server(gauges, [1e-2, 1e-1], workers=1, batch_max=4)
+    key = {}
+    try:
+        for i in range(14):
+            gi, m = (0, 1e-2) if i < 10 else (1, 1e-1)
+            key[i] = (gi, m)
+            srv.submit(i, gi, m, np.full(256, float(i), dtype=complex))
+        srv.drain()
+        assert sorted(r.rid for r in srv.done) == list(range(14))
+        for r in srv.done:
+            assert r.stats["converged"] and np.allclose(r.x, r.b / r.mass)
+        assert all(len(ids) <= 4 for _, ids in fake.batches)
+        for mass, ids in fake.batches:      # one hierarchy per call
+            assert len({key[i] for i in ids}) == 1 and key[ids[0]][1] == mass
+        s = serve.latency_summary(srv.done)
+        assert s["mean_batch"] > 1.0
+        one = serve.hierarchy_bytes(16, [(4, 4), (2, 2)], [24, 32], True)
+        assert srv._footprint(0) == one + serve.batch_workspace_bytes(16, [(4, 4), (2, 2)], [24, 32])
     finally:
         srv.close()
