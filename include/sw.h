@@ -245,21 +245,21 @@ int sw_mg_transfer(sw_mg* mg, int level, int dir, const void* in, void* out, int
 
 /* Schur operator without any device allocation.  The paper has no
  * counterpart: this is a deployment variant of sw_dslash(..., SW_OP_S,
- * SW_PREC_FP64, ...) for callers that cannot call cudaMalloc -- code running
- * while a stream is captured into a CUDA graph, or inside a framework that
- * owns all device memory.  Same result as sw_dslash with SW_OP_S (odd-block
- * entries of out written as 0).
+ * SW_PREC_FP64, ...) for callers that cannot call cudaMalloc -- applications
+ * or frameworks that own every device allocation of the process, or loops
+ * that must not enter the allocator.  Same result as sw_dslash with SW_OP_S
+ * (odd-block entries of out written as 0).
  *  in, out  device pointers to complex128 [L1][L0] fields (no host path).
  *  Scratch  a fixed file-scope device array of 7 x 65536 complex128 (7.3 MB),
  *           held by every GPU that loads the library until the process exits;
  *           lattices with more than 65536 sites are rejected with
  *           SW_ERR_SHAPE.  The B^-1 table is rebuilt from the links on every
  *           call.
- *  The first call on a device looks up the scratch address on that device;
- *  make that first call before any stream capture.  All calls share the one
- *  array, which keeps the previous call's contents: calls that overlap on the
- *  GPU (other streams, other contexts of the same device) race.  Asynchronous
- *  on the context stream. */
+ *  The first call on a device looks up the scratch address on that device
+ *  (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  All calls share the one array, which keeps the previous call's contents:
+ *  calls that overlap on the GPU (other streams, other contexts of the same
+ *  device) race.  Asynchronous on the context stream. */
 int sw_dslash_schur_noalloc(sw_gauge* g, double mass, const void* in, void* out);
 
 /* Measurement support.

@@ -148,13 +148,36 @@ def _same_place(*arrs):
     return places.pop()
 
 
+def _dtype_name(a) -> str:
+    if isinstance(a, np.ndarray):
+        return a.dtype.name
+    return str(a.dtype).replace("torch.", "")
+
+
+def _check_buf(h, a, numel: int, dtype: str = "complex128", what: str = "buffer"):
+    """Rejects, before the library sees its pointer, a buffer of the wrong
+    element type or size, or a device tensor on another GPU than the one the
+    handle's context uses: the kernels would otherwise read or write outside it."""
+    if _dtype_name(a) != dtype:
+        raise ValueError(f"{what}: expected {dtype}, got {_dtype_name(a)}")
+    n = int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+    if n != numel:
+        raise ValueError(f"{what}: expected {numel} elements, got {n}")
+    if not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False):
+        dev = getattr(h, "device", None)
+        if dev is not None and a.device.index != dev:
+            raise ValueError(f"{what}: tensor is on cuda:{a.device.index}, the context on cuda:{dev}")
+
+
 def sw_context_create(device: int = 0, stream=None) -> _Handle:
     """stream: a raw cudaStream_t value (e.g. torch.cuda.current_stream().cuda_stream) or None."""
     out = _VP()
     rc = lib().sw_context_create(device, stream or None, ctypes.byref(out))
     if rc != 0:
         raise SwError(rc, "sw_context_create failed")
-    return _Handle(out, out, lib().sw_context_free)
+    h = _Handle(out, out, lib().sw_context_free)
+    h.device = int(device)
+    return h
 
 
 def sw_context_free(ctx: _Handle):
@@ -167,12 +190,16 @@ def sw_last_error(ctx: _Handle) -> str:
 
 def sw_gauge_load(ctx: _Handle, theta) -> _Handle:
     """theta: float64 [2, L1, L0] link angles (numpy or torch CUDA tensor)."""
+    if len(theta.shape) != 3 or int(theta.shape[0]) != 2:
+        raise ValueError("theta must have shape [2, L1, L0]")
     L1, L0 = int(theta.shape[1]), int(theta.shape[2])
+    _check_buf(ctx, theta, 2 * L0 * L1, "float64", "theta")
     p, dev = _ptr(theta)
     out = _VP()
     _check(lib().sw_gauge_load(ctx.ptr, L0, L1, p, dev, ctypes.byref(out)), ctx.ptr)
     h = _Handle(out, ctx.ptr, lib().sw_gauge_free)
     h.shape = (L1, L0)
+    h.device = getattr(ctx, "device", None)
     return h
 
 
@@ -182,6 +209,10 @@ def sw_gauge_free(g: _Handle):
 
 def sw_dslash(g: _Handle, mass: float, op: int, precision: int, inp, out):
     dev = _same_place(inp, out)
+    dt = "complex64" if precision == SW_PREC_FP32 else "complex128"
+    N = g.shape[0] * g.shape[1]
+    _check_buf(g, inp, N, dt, "in")
+    _check_buf(g, out, N, dt, "out")
     _check(lib().sw_dslash(g.ptr, float(mass), op, precision, _ptr(inp)[0], _ptr(out)[0], dev),
            g.ctx_ptr)
     return out
@@ -197,21 +228,35 @@ def sw_mg_setup(g: _Handle, mass: float, levels: int, block, nvec, params=None, 
                 psi0=None) -> _Handle:
     """block: [(b0, b1)] * (levels-1); nvec: [nv] * (levels-1); psi0: None or a list
     of numpy complex128 arrays [nvec[l], ndof_l] (vector-major)."""
+    if len(block) != levels - 1 or len(nvec) != levels - 1:
+        raise ValueError("block and nvec need one entry per level below the fine one")
     blk = (_I * (2 * (levels - 1)))(*[int(v) for b in block for v in b])
     nv = (_I * (levels - 1))(*[int(v) for v in nvec])
     keep = []
     ps = None
     if psi0 is not None:
+        if len(psi0) != levels - 1:
+            raise ValueError("psi0 needs one array per level below the coarsest")
         ps = (_VP * (levels - 1))()
+        L1, L0 = g.shape
+        E0, E1, ndof = L0, L1, L0 * L1
         for l, arr in enumerate(psi0):
             a = np.ascontiguousarray(arr, dtype=np.complex128)
+            if a.size != int(nvec[l]) * ndof:
+                raise ValueError(f"psi0[{l}]: expected {int(nvec[l])} x {ndof} elements, got {a.size}")
             keep.append(a)
             ps[l] = a.ctypes.data
+            b0, b1 = block[l]
+            E0, E1 = (E0 // (2 * b0), E1 // (2 * b1)) if l == 0 else (E0 // b0, E1 // b1)
+            ndof = E0 * E1 * 2 * int(nvec[l])
     out = _VP()
     prm = ctypes.byref(params) if params is not None else None
     _check(lib().sw_mg_setup(g.ptr, float(mass), levels, blk, nv, prm, seed, ps,
                              ctypes.byref(out)), g.ctx_ptr)
-    return _Handle(out, g.ctx_ptr, lib().sw_mg_free)
+    h = _Handle(out, g.ctx_ptr, lib().sw_mg_free)
+    h.shape = g.shape
+    h.device = getattr(g, "device", None)
+    return h
 
 
 def sw_mg_free(mg: _Handle):
@@ -220,6 +265,9 @@ def sw_mg_free(mg: _Handle):
 
 def sw_mg_solve(mg: _Handle, b, x, tol: float, allow_noconv: bool = False) -> dict:
     dev = _same_place(b, x)
+    N = mg.shape[0] * mg.shape[1]
+    _check_buf(mg, b, N, what="b")
+    _check_buf(mg, x, N, what="x")
     st = sw_solve_stats()
     rc = _check(lib().sw_mg_solve(mg.ptr, _ptr(b)[0], _ptr(x)[0], float(tol), dev,
                                   ctypes.byref(st)), mg.ctx_ptr,
@@ -232,6 +280,9 @@ def sw_mg_solve(mg: _Handle, b, x, tol: float, allow_noconv: bool = False) -> di
 def sw_mg_solve_batch(mg: _Handle, B, X, tol: float, allow_noconv: bool = False):
     dev = _same_place(B, X)
     nrhs = int(B.shape[0])
+    N = mg.shape[0] * mg.shape[1]
+    _check_buf(mg, B, nrhs * N, what="B")
+    _check_buf(mg, X, nrhs * N, what="X")
     st = (sw_solve_stats * max(nrhs, 1))()
     _check(lib().sw_mg_solve_batch(mg.ptr, nrhs, _ptr(B)[0], _ptr(X)[0], float(tol), dev, st),
            mg.ctx_ptr, allow=(-4,) if allow_noconv else ())
@@ -271,8 +322,16 @@ def sw_mg_export_Y(mg: _Handle, level: int) -> np.ndarray:
     return Y
 
 
+def _level_len(mg: _Handle, level: int) -> int:
+    e0, e1, nc = sw_mg_level_info(mg, level)
+    return e0 * e1 * nc
+
+
 def sw_mg_apply_level(mg: _Handle, level: int, precision: int, dagger: int, inp, out):
     dev = _same_place(inp, out)
+    n = _level_len(mg, level)
+    _check_buf(mg, inp, n, what="in")
+    _check_buf(mg, out, n, what="out")
     _check(lib().sw_mg_apply_level(mg.ptr, level, precision, dagger, _ptr(inp)[0], _ptr(out)[0],
                                    dev), mg.ctx_ptr)
     return out
@@ -280,6 +339,9 @@ def sw_mg_apply_level(mg: _Handle, level: int, precision: int, dagger: int, inp,
 
 def sw_mg_transfer(mg: _Handle, level: int, direction: int, inp, out):
     dev = _same_place(inp, out)
+    nf, nc = _level_len(mg, level), _level_len(mg, level + 1)
+    _check_buf(mg, inp, nf if direction == 0 else nc, what="in")
+    _check_buf(mg, out, nc if direction == 0 else nf, what="out")
     _check(lib().sw_mg_transfer(mg.ptr, level, direction, _ptr(inp)[0], _ptr(out)[0], dev),
            mg.ctx_ptr)
     return out
@@ -312,6 +374,9 @@ def sw_dslash_schur_noalloc(g: _Handle, mass: float, inp, out):
     p_out, d_out = _ptr(out)
     if not (d_in and d_out):
         raise ValueError("sw_dslash_schur_noalloc takes device buffers only")
+    N = g.shape[0] * g.shape[1]
+    _check_buf(g, inp, N, what="in")
+    _check_buf(g, out, N, what="out")
     _check(lib().sw_dslash_schur_noalloc(g.ptr, float(mass), p_in, p_out), g.ctx_ptr)
     return out
 
@@ -325,6 +390,9 @@ def sw_cg_eo_solve(g: _Handle, mass: float, b, x, tol: float, maxiter: int = 100
                    allow_noconv: bool = False) -> dict:
     """CG on the even/odd normal system (the paper's comparison solver)."""
     dev = _same_place(b, x)
+    N = g.shape[0] * g.shape[1]
+    _check_buf(g, b, N, what="b")
+    _check_buf(g, x, N, what="x")
     st = sw_solve_stats()
     rc = _check(lib().sw_cg_eo_solve(g.ptr, float(mass), _ptr(b)[0], _ptr(x)[0], float(tol),
                                      int(maxiter), dev, ctypes.byref(st)), g.ctx_ptr,

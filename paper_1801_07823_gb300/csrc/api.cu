@@ -62,30 +62,6 @@ T* dmalloc(size_t count) {
   return (T*)p;
 }
 
-int fail(sw_ctx* c, const SwError& e) {
-  if (c) c->err = e.msg;
-  return e.code;
-}
-
-template <typename F>
-int guarded(sw_ctx* c, F&& f) {
-  try {
-    if (c) {
-      c->err.clear();
-      SW_CUDA(cudaSetDevice(c->device));
-    }
-    // A non-sticky error left by an earlier unchecked runtime call of the
-    // process would otherwise surface at this call's first launch check.
-    cudaError_t stale = cudaGetLastError();
-    if (stale != cudaSuccess) report_stale_error(stale);
-    return f();
-  } catch (const SwError& e) {
-    return fail(c, e);
-  } catch (const std::bad_alloc&) {
-    return fail(c, SwError{SW_ERR_OOM, "host allocation failed"});
-  }
-}
-
 void gauge_binv(sw_gauge* g, double mass) {
   if (!g->binv) g->binv = dmalloc<double2>((size_t)g->N * 4);
   if (g->binv_mass != mass) {

@@ -1,9 +1,10 @@
 // sw_dslash_schur_noalloc: the Schur operator of sw_dslash (SW_OP_S) for
-// callers that must not allocate device memory -- for instance code that runs
-// while a CUDA stream is being captured into a graph, or inside a framework
-// that owns every device allocation and forbids others.  sw_dslash allocates
-// its work buffers and the B^-1 table on first use; this entry point instead
-// keeps all of its scratch in one file-scope device array of fixed size.
+// callers that must not allocate device memory -- for instance a host
+// application or framework that owns every device allocation and forbids
+// others, or a real-time loop that may not call into the allocator.
+// sw_dslash allocates its work buffers and the B^-1 table on first use; this
+// entry point instead keeps all of its scratch in one file-scope device array
+// of fixed size.
 //
 // Scratch layout for N = L0 L1 <= kNoAllocMaxSites (complex128 units):
 //   [0, N)      input packed to parity-split order
@@ -43,9 +44,7 @@ double2* noalloc_scratch(int device) {
 extern "C" int sw_dslash_schur_noalloc(sw_gauge* g, double mass, const void* in, void* out) {
   if (!g || !in || !out) return SW_ERR_ARG;
   sw_ctx* c = g->ctx;
-  try {
-    c->err.clear();
-    SW_CUDA(cudaSetDevice(c->device));
+  return guarded(c, [&] {
     SW_REQUIRE((long)g->N <= kNoAllocMaxSites, SW_ERR_SHAPE,
                "sw_dslash_schur_noalloc: lattice has " + std::to_string(g->N) +
                    " sites, the fixed scratch holds at most " +
@@ -64,8 +63,5 @@ extern "C" int sw_dslash_schur_noalloc(sw_gauge* g, double mass, const void* in,
     SW_CUDA(cudaMemsetAsync(b + N / 2, 0, N / 2 * sizeof(double2), s));
     launch_unpack(g, b, (double2*)out, s);
     return SW_OK;
-  } catch (const SwError& e) {
-    c->err = e.msg;
-    return e.code;
-  }
+  });
 }

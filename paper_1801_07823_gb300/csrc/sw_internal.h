@@ -3,6 +3,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -33,6 +35,13 @@ void dev_free(void* p, const char* what);
 // Notes on stderr (first few times) that an entry point cleared a pending
 // error of an earlier, unchecked runtime call of the process.
 void report_stale_error(cudaError_t e);
+// Body of every extern "C" entry point: makes the context's device current,
+// clears (and reports) a non-sticky error left pending by an earlier unchecked
+// runtime call of the process, runs f, and turns every C++ exception into an
+// SW_ERR_* code with the message kept in the context.
+inline int fail(sw_ctx* c, int code, const std::string& msg);
+template <typename F>
+int guarded(sw_ctx* c, F&& f);
 #define SW_REQUIRE(cond, code, text)                 \
   do {                                               \
     if (!(cond)) throw SwError{(code), (text)};      \
@@ -119,6 +128,30 @@ struct sw_gauge {
   double2* binv_naik = nullptr;  // B_Naik^-1 for naik_mass
   double2* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // [N] scratch for sw_dslash
 };
+
+// ------------------------------------------------------------- entry guard
+inline int fail(sw_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+template <typename F>
+int guarded(sw_ctx* c, F&& f) {
+  try {
+    if (c) {
+      c->err.clear();
+      SW_CUDA(cudaSetDevice(c->device));
+    }
+    cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) report_stale_error(stale);
+    return f();
+  } catch (const SwError& e) {
+    return fail(c, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(c, SW_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(c, SW_ERR_CUDA, std::string("unexpected host error: ") + e.what());
+  }
+}
 
 // ------------------------------------------------------------- geometry
 // Parity-split block-major order of a fine field: f = par * N/2 + 4 * hb + k,

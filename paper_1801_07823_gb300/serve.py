@@ -114,6 +114,9 @@ class Server:
                  blocks=((4, 4), (2, 2)), nvec=(24, 32), params=None, device=0, psi0_fn=None,
                  batch_max=1):
         import torch
+        if int(batch_max) > 1 and not mixed:
+            raise ValueError("batch_max > 1 needs mixed=True: sw_mg_solve_batch batches the "
+                             "coarsest solves of mixed-precision hierarchies only")
         self.torch = torch
         self.gauges = gauges
         self.masses = np.array(sorted(masses))

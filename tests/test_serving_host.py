@@ -177,3 +177,13 @@ def test_requests_on_one_hierarchy_are_batched(fake):
         assert srv._footprint(0) == one + serve.batch_workspace_bytes(16, [(4, 4), (2, 2)], [24, 32])
     finally:
         srv.close()
+
+
+def test_batching_on_fp64_hierarchies_is_rejected(fake):
+    """sw_mg_solve_batch batches mixed-precision hierarchies only, so a server
+    that would batch FP64 hierarchies is refused when it is built, instead of
+    failing every request later."""
+    with pytest.raises(ValueError):
+        serve.Server(_gauges(n=1), [1e-2], workers=1, mixed=False, batch_max=4)
+    srv = serve.Server(_gauges(n=1), [1e-2], workers=1, mixed=False, batch_max=1)
+    srv.close()

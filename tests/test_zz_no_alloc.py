@@ -1,8 +1,9 @@
 """The allocation-free Schur operator against sw_dslash(SW_OP_S).
 
-sw_dslash_schur_noalloc serves callers that cannot call cudaMalloc (work
-queued during CUDA graph capture, frameworks that own all device memory); it
-keeps its scratch in a fixed device array.  This file is collected last so a
+sw_dslash_schur_noalloc serves callers that cannot call cudaMalloc
+(applications or frameworks that own every device allocation of the process,
+loops that must not enter the allocator); it keeps its scratch in a fixed
+device array.  This file is collected last so a
 run that stops at the first failure has run every other test first.
 """
 import numpy as np
