@@ -171,53 +171,65 @@ class Hierarchy:
             ext = cext
 
     # ---- solve -------------------------------------------------------------
+    # The steps of the solve are methods, in the paper's order, so that each
+    # can be read (and a test can swap one for a deliberately wrong variant).
+    def fine_schur(self, v):
+        """The level-1 operator of the solve, I - A_eo A_oe (one fine mat-vec)."""
+        self.st["fine_applies"] += 1
+        return self.F.schur(v)
+
+    def solve_level(self, l, rhs):
+        """Approximate solve on level l >= 1 (Sec. IV, Table kcycle): GCR on A_hat
+        preconditioned by the next K-cycle on intermediate levels, CGNE on the
+        coarsest level."""
+        p, lev = self.p, self.levels[l]
+        op = lambda v: lev.op @ v
+        if l == len(self.levels) - 1:
+            e, k = krylov.cgne(op, lambda v: lev.opdag @ v, rhs, p.coarsest_tol, p.coarsest_maxiter)
+            self.st["coarsest_iters"] += k
+            self.st["coarsest_solves"] += 1
+            return e
+        e, k, _, _ = krylov.fgcr(op, lambda r: self.kcycle(l, r), rhs, p.inter_tol * norm(rhs),
+                                 p.inter_restart, p.inter_maxiter, confirm=False)
+        self.st["inter_iters"] += k
+        self.st["inter_solves"] += 1
+        return e
+
+    def kcycle(self, l, r):
+        """K-cycle of an intermediate level l: (1) MR pre-smoother, (2) coarse
+        correction P A_hat^-1 P^dag on the smoothed residual, (3) MR post-smoother
+        on the residual left after steps 1 and 2."""
+        p, lev = self.p, self.levels[l]
+        op = lambda v: lev.op @ v
+        x1, r1 = krylov.mr(op, r, p.smoother_iters, p.omega)
+        ehat = self.solve_level(l + 1, lev.P.conj().T @ r1)
+        e = lev.P @ ehat
+        r2 = r1 - op(e)
+        x3, _ = krylov.mr(op, r2, p.smoother_iters, p.omega)
+        return x1 + e + x3
+
+    def kcycle_fine(self, r):
+        """K-cycle of the fine level on the even half (Sec. IV): the same three
+        steps with S, restricting (r1, 0) (odd contributions set to zero) and
+        keeping the even part of the prolonged error."""
+        F, p = self.F, self.p
+        S = self.fine_schur
+        x1, r1 = krylov.mr(S, r, p.smoother_iters, p.omega)
+        full = np.zeros(F.N, dtype=complex)
+        full[F.even] = r1
+        ehat = self.solve_level(1, self.levels[0].P.conj().T @ full)
+        e = (self.levels[0].P @ ehat)[F.even]
+        r2 = r1 - S(e)
+        x3, _ = krylov.mr(S, r2, p.smoother_iters, p.omega)
+        return x1 + e + x3
+
     def solve(self, b: np.ndarray, tol: float, on_outer=None):
         """Solve D x = b (b as [N] complex, site order x0 + L0 x1) to
         ||b - D x|| <= tol ||b||.  Returns (x, stats dict)."""
         F, p = self.F, self.p
-        st = dict(fine_applies=0, inter_iters=0, inter_solves=0, coarsest_iters=0,
-                  coarsest_solves=0)
-
-        def S(v):
-            st["fine_applies"] += 1
-            return F.schur(v)
-
+        self.st = st = dict(fine_applies=0, inter_iters=0, inter_solves=0, coarsest_iters=0,
+                            coarsest_solves=0)
         nlev = len(self.levels)
-
-        def solve_level(l, rhs):
-            lev = self.levels[l]
-            op = lambda v: lev.op @ v
-            if l == nlev - 1:
-                e, k = krylov.cgne(op, lambda v: lev.opdag @ v, rhs, p.coarsest_tol, p.coarsest_maxiter)
-                st["coarsest_iters"] += k
-                st["coarsest_solves"] += 1
-                return e
-            e, k, _, _ = krylov.fgcr(op, lambda r: kcycle(l, r), rhs, p.inter_tol * norm(rhs),
-                                     p.inter_restart, p.inter_maxiter, confirm=False)
-            st["inter_iters"] += k
-            st["inter_solves"] += 1
-            return e
-
-        def kcycle(l, r):
-            lev = self.levels[l]
-            op = lambda v: lev.op @ v
-            x1, r1 = krylov.mr(op, r, p.smoother_iters, p.omega)
-            ehat = solve_level(l + 1, lev.P.conj().T @ r1)
-            e = lev.P @ ehat
-            r2 = r1 - op(e)
-            x3, _ = krylov.mr(op, r2, p.smoother_iters, p.omega)
-            return x1 + e + x3
-
-        def kcycle_fine(r):
-            x1, r1 = krylov.mr(S, r, p.smoother_iters, p.omega)
-            full = np.zeros(F.N, dtype=complex)
-            full[F.even] = r1                      # odd contributions set to zero
-            ehat = solve_level(1, self.levels[0].P.conj().T @ full)
-            e = (self.levels[0].P @ ehat)[F.even]  # odd part of the prolonged error dropped
-            r2 = r1 - S(e)
-            x3, _ = krylov.mr(S, r2, p.smoother_iters, p.omega)
-            return x1 + e + x3
-
         bn = norm(b)
         if self.fine_op == "D":
             def Dop(v):
@@ -226,7 +238,7 @@ class Hierarchy:
 
             def kcycle_D(r):
                 x1, r1 = krylov.mr(Dop, r, p.smoother_iters, p.omega)
-                ehat = solve_level(1, self.levels[0].P.conj().T @ r1)
+                ehat = self.solve_level(1, self.levels[0].P.conj().T @ r1)
                 e = self.levels[0].P @ ehat
                 r2 = r1 - Dop(e)
                 x3, _ = krylov.mr(Dop, r2, p.smoother_iters, p.omega)
@@ -238,9 +250,9 @@ class Hierarchy:
                       true_resid=norm(b - F.D @ x) / bn)
             return x, st
         bt = F.schur_rhs(b)
-        precond = kcycle_fine if nlev > 1 else (lambda r: r)
-        ze, it, rs, conv = krylov.fgcr(S, precond, bt, tol * bn, p.outer_restart, p.outer_maxiter,
-                                       confirm=True, on_iter=on_outer)
+        precond = self.kcycle_fine if nlev > 1 else (lambda r: r)
+        ze, it, rs, conv = krylov.fgcr(self.fine_schur, precond, bt, tol * bn, p.outer_restart,
+                                       p.outer_maxiter, confirm=True, on_iter=on_outer)
         x = F.reconstruct(b, ze)
         st.update(outer_iters=it, restarts=rs, converged=conv,
                   true_resid=norm(b - F.D @ x) / bn)
