@@ -100,8 +100,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision solve measured beside the FP64 one")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="K",
+                    help="run only K-right-hand-side batched solves on the mixed hierarchy "
+                         "(one warm-up and --batch-reps timed batches; for profiling)")
     ap.add_argument("--dslash-only", action="store_true",
                     help="run only the Dslash bandwidth microbenchmark")
+    ap.add_argument("--batch-reps", type=int, default=3,
+                    help="timed batches per batch width")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving measurement (0: skip it)")
     return ap.parse_args()
@@ -339,6 +344,58 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batched_measurement(sw, ctx, hm, nbat, L, rank, world, flush, stream, barrier, fp64_value,
+                        xref, reps=3):
+    """nbat right-hand sides per sw_mg_solve_batch call on the mixed hierarchy hm:
+    one warm-up batch (workspace, autotuner), then `reps` timed batches of fresh
+    right-hand sides, L2 flushed before each.  Reports solves/s, the coarsest
+    kernel's share and time per iteration, and the largest relative difference
+    of the first solutions from the FP64 hierarchy's solutions of the same
+    right-hand sides."""
+    import torch
+    tol = WORKLOAD["tol"]
+    mk = lambda off: torch.stack([torch.from_numpy(rhs(rhs_seed(rank, k, off), L))
+                                  for k in range(nbat)]).cuda()
+    BB = mk(500)
+    XB = torch.zeros_like(BB)
+    sw.sw_mg_solve_batch(hm, BB, XB, tol)  # warm-up
+    err = max(float(torch.linalg.norm(XB[k] - xref[k]) / torch.linalg.norm(xref[k]))
+              for k in xref)
+    batches = [mk(600 + 100 * j) for j in range(reps)]
+    barrier()
+    sw.sw_set_timing(ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sts, ms = [], 0.0
+    for Bj in batches:
+        flush.zero_()
+        e0.record(stream)
+        sts += sw.sw_mg_solve_batch(hm, Bj, XB, tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    bk = sw.sw_kernel_times(ctx, 7)
+    sw.sw_set_timing(ctx, False)
+    barrier()
+    sec = max_over_ranks(ms / 1e3, world)
+    val = job_rate(world, nbat * reps, sec)
+    return {
+        "value": val, "unit": UNIT, "width": nbat, "batches": reps,
+        "ms_per_batch": sec / reps * 1e3,
+        "dtype": "f64 outer FGCR, vectors and Krylov scalars; f32 fine smoother; f16 (scaled) "
+                 "level-2 stencil; coarsest stencil products tf32 on the tensor cores (f32 "
+                 "with SW_BATCH_FP32=1), f64 iterates",
+        "converged_all": all(x_["converged"] and x_["true_resid"] <= tol for x_ in sts),
+        "true_resid_max": max(x_["true_resid"] for x_ in sts),
+        "rel_err_vs_fp64_solve_max": err,
+        "outer_iters_max": max(x_["outer_iters"] for x_ in sts),
+        "coarsest_avg": float(np.mean([x_["coarsest_iters"] / max(x_["coarsest_solves"], 1)
+                                       for x_ in sts])),
+        "coarsest_kernel": {"launches": bk[5][0], "ms": bk[5][1], "iterations": bk[6][0],
+                            "us_per_iteration": 1e3 * bk[5][1] / max(bk[6][0], 1),
+                            "share": bk[5][1] / max(ms, 1e-9)},
+        "speedup_vs_fp64": val / fp64_value}
+
+
 # ---------------------------------------------------------------------------- native
 def run_native(args, rank, world, local):
     import torch
@@ -477,47 +534,47 @@ def run_native(args, rank, world, local):
         mel = e0_.elapsed_time(e1_) / 1e3
         mel = max_over_ranks(mel, world)
         m0 = mt[0]
+        xa, xb = torch.zeros_like(B[0]), torch.zeros_like(B[0])
+        sw.sw_mg_solve(h, B[0], xa, WORKLOAD["tol"])
+        sw.sw_mg_solve(hm, B[0], xb, WORKLOAD["tol"])
+        merr = float(torch.linalg.norm(xb - xa) / torch.linalg.norm(xa))
         variants["mixed"] = {
             "value": job_rate(world, args.steps, mel), "unit": UNIT, "ms_per_step": mel / args.steps * 1e3,
             "dtype": "f64 outer FGCR and vectors; f32 fine smoother; f16 (scaled) level-2 "
                      "stencil; double-float coarsest stencil",
             "converged_all": all(x_["converged"] and x_["true_resid"] <= WORKLOAD["tol"] for x_ in mt),
             "true_resid_max": max(x_["true_resid"] for x_ in mt), "setup_s": msetup,
+            "rel_err_vs_fp64_solve": merr,
             "outer_iters": m0["outer_iters"],
             "inter_avg": m0["inter_iters"] / max(m0["inter_solves"], 1),
             "coarsest_avg": m0["coarsest_iters"] / max(m0["coarsest_solves"], 1),
             "speedup_vs_fp64": job_rate(world, args.steps, mel) / value}
-        # batched: 16 right-hand sides per sw_mg_solve_batch call on the same mixed
-        # hierarchy (lockstep K-cycle, one batched FP32 coarsest CGNE per level visit)
-        nbat = 16
-        BB = torch.stack([torch.from_numpy(rhs(rhs_seed(rank, k, 500), L)) for k in range(nbat)]).cuda()
-        XB = torch.zeros_like(BB)
-        sw.sw_mg_solve_batch(hm, BB, XB, WORKLOAD["tol"])  # warm-up (allocates the workspace)
-        barrier()
-        flush.zero_()
-        sw.sw_set_timing(ctx, True)
-        e0_.record(stream)
-        bt = sw.sw_mg_solve_batch(hm, BB, XB, WORKLOAD["tol"])
-        e1_.record(stream)
-        barrier()
-        bel = e0_.elapsed_time(e1_) / 1e3
-        bk = sw.sw_kernel_times(ctx, 7)
-        sw.sw_set_timing(ctx, False)
-        bel = max_over_ranks(bel, world)
-        variants["batched16_mixed"] = {
-            "value": job_rate(world, nbat, bel), "unit": UNIT, "ms_per_batch": bel * 1e3,
-            "dtype": "f64 outer FGCR and vectors; f32 fine smoother; f16 (scaled) level-2 "
-                     "stencil; f32 batched coarsest stencil",
-            "converged_all": all(x_["converged"] and x_["true_resid"] <= WORKLOAD["tol"] for x_ in bt),
-            "true_resid_max": max(x_["true_resid"] for x_ in bt),
-            "outer_iters_max": max(x_["outer_iters"] for x_ in bt),
-            "coarsest_avg": float(np.mean([x_["coarsest_iters"] / max(x_["coarsest_solves"], 1)
-                                           for x_ in bt])),
-            "coarsest_kernel": {"launches": bk[5][0], "ms": bk[5][1],
-                                "iterations": bk[6][0],
-                                "us_per_iteration": 1e3 * bk[5][1] / max(bk[6][0], 1),
-                                "share": bk[5][1] / (bel * 1e3)},
-            "speedup_vs_fp64": job_rate(world, nbat, bel) / value}
+        # batched: 16, 32 and 64 right-hand sides per sw_mg_solve_batch call on the
+        # same mixed hierarchy (lockstep K-cycle, one batched coarsest CGNE on the
+        # tensor cores per level visit), each width timed over `reps` batches
+        xref = {}
+        for k in range(3):  # FP64 solutions of the first right-hand sides: error reference
+            xk = torch.zeros_like(B[0])
+            bk0 = torch.from_numpy(rhs(rhs_seed(rank, k, 500), L)).cuda()
+            sw.sw_mg_solve(h, bk0, xk, WORKLOAD["tol"])
+            xref[k] = xk.clone()
+        variants["batched"] = {}
+        for nbat in (16, 32, 64):
+            variants["batched"][str(nbat)] = batched_measurement(
+                sw, ctx, hm, nbat, L, rank, world, flush, stream, barrier, value, xref,
+                reps=args.batch_reps)
+        best = max(variants["batched"].values(), key=lambda v: v["value"])
+        variants["batched_best"] = {"value": best["value"], "unit": UNIT, "width": best["width"],
+                                    "speedup_vs_fp64": best["value"] / value}
+        variants["autotune"] = [dict(zip(("nc", "K", "sites", "stages", "us_per_iter"), e))
+                                for e in sw.sw_autotune_entries()]
+        # the CUDA-core FP32 batched kernel on a second mixed hierarchy, for comparison
+        os.environ["SW_BATCH_FP32"] = "1"
+        hf = sw.sw_mg_setup(g, m, 3, WORKLOAD["blocks"], WORKLOAD["nvec"], params=pm, psi0=psi0)
+        variants["batched_cuda_core_16"] = batched_measurement(
+            sw, ctx, hf, 16, L, rank, world, flush, stream, barrier, value, xref, reps=2)
+        os.environ.pop("SW_BATCH_FP32")
+        hf.free()
         hm.free()
         # the paper's comparison solver on the same system: CG on the even/odd
         # normal equations (Sec. II, Fig. iterworst), FP64
@@ -601,6 +658,31 @@ def main():
         torch.cuda.set_device(local)
         ctx = sw.sw_context_create(local, torch.cuda.current_stream().cuda_stream)
         print(json.dumps({"dslash": dslash_bandwidth(sw, ctx)}), flush=True)
+        ctx.free()
+        return
+    if args.batched_only:
+        import torch
+        import paper_1801_07823_gb300 as sw
+        from paper_1801_07823_gb300 import presets
+        torch.cuda.set_device(local)
+        stream = torch.cuda.current_stream()
+        ctx = sw.sw_context_create(local, stream.cuda_stream)
+        th, psi0 = gauge_and_psi0(args.L, WORKLOAD["beta"], args.sweeps, "cuda")
+        g = sw.sw_gauge_load(ctx, th)
+        pm = presets.make_params(sw, presets.FP64_256)
+        pm.precision = sw.SW_MG_MIXED
+        hm = sw.sw_mg_setup(g, WORKLOAD["mass"], 3, WORKLOAD["blocks"], WORKLOAD["nvec"],
+                            params=pm, psi0=psi0)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        xref = {0: torch.zeros(args.L * args.L, dtype=torch.complex128, device="cuda")}
+        sw.sw_mg_solve(hm, torch.from_numpy(rhs(rhs_seed(rank, 0, 500), args.L)).cuda(),
+                       xref[0], WORKLOAD["tol"])
+        out = batched_measurement(sw, ctx, hm, args.batched_only, args.L, rank, world, flush,
+                                  stream, torch.cuda.synchronize, 1.0, xref, reps=args.batch_reps)
+        out["autotune"] = sw.sw_autotune_entries()
+        print(json.dumps({"batched": out}), flush=True)
+        hm.free()
+        g.free()
         ctx.free()
         return
     if args.impl == "reference":

@@ -81,9 +81,9 @@ typedef struct {
                             SW_MG_MIXED: setup, Gram-Schmidt, coarse-operator build,
                             the outer FGCR (its S, residuals, restarts) and all
                             vectors and Krylov recurrences stay FP64; inside the
-                            K-cycle the fine S runs in FP32, intermediate-level
-                            stencils in FP16S, and the coarsest CGNE applies its
-                            stencil in DF64. */
+                            K-cycle the fine S runs in FP32 and intermediate-level
+                            stencils in FP16S; the coarsest CGNE stays FP64
+                            (environment SW_COARSEST_DF64=1: its stencil in DF64). */
   int fine_operator;     /* SW_MG_COARSEN_A (default): the paper's method, Galerkin
                             coarsening of A = D B^-1 with the Schur outer solve.
                             SW_MG_COARSEN_D: the same recipe applied to D itself
@@ -181,11 +181,14 @@ int sw_mg_solve(sw_mg* mg, const void* b, void* x, double tol, int on_device,
  * [nrhs] (or NULL).  Each right-hand side converges on its own (own Krylov
  * scalars and stopping tests, the same stopping rule as sw_mg_solve).  On an
  * SW_MG_FP64 hierarchy the solves run one after the other.  On an SW_MG_MIXED
- * hierarchy up to 16 right-hand sides advance together through the K-cycle
+ * hierarchy up to 64 right-hand sides advance together through the K-cycle
  * and the coarsest-level solves of all of them run in one batched kernel that
- * reads the coarsest stencil once per batch, in FP32 (stencil products and
- * their sums; iterates and Krylov scalars FP64); the outer FGCR stays FP64.
- * A right-hand side's result does not depend on the others in its batch.
+ * reads the coarsest stencil once per batch: its stencil products run on the
+ * tensor cores (tcgen05, TF32 operands, FP32 accumulation) for coarse dof
+ * counts 16, 24, 32, 48 and 64, with a pipeline depth picked by timing on
+ * first use (sw_autotune_entries); iterates and Krylov scalars stay FP64, and
+ * so does the outer FGCR.  Larger nrhs run in groups of 64.  A right-hand
+ * side's scalars do not depend on the others in its batch.
  * Returns SW_ERR_NOCONV if any right-hand side did not converge. */
 int sw_mg_solve_batch(sw_mg* mg, int nrhs, const void* B, void* X, double tol, int on_device,
                       sw_solve_stats* st);
@@ -290,6 +293,22 @@ long long sw_launch_count(void);
  * every other CTA's bounded wait runs out (about a second).  Expected result:
  * SW_ERR_TIMEOUT, with the context still usable afterwards. */
 int sw_debug_cgne_stall(sw_mg* mg);
+
+/* Failure-detection check of the batched coarsest kernel: runs it once on
+ * nrhs zero right-hand sides with one CTA withholding its first grid-barrier
+ * arrival, so every other CTA's bounded wait runs out (about a second).
+ * Expected result: SW_ERR_TIMEOUT, with the context still usable afterwards. */
+int sw_debug_batch_stall(sw_mg* mg, int nrhs);
+
+/* Choices of the autotuner in this process: entry k gives the coarse dof per
+ * site nc[k], the batch width K[k], the number of coarse sites, the choice and
+ * its measured microseconds per CGNE iteration.  For the batched tensor-core
+ * coarsest kernel (K = 8, 16, 32 or 64) the choice is its pipeline depth; for
+ * the single-right-hand-side FP64 coarsest kernel (K = 1) it is the product
+ * form (0: four real FMAs per complex multiply-add, 1: three, with a stored
+ * sum plane).  Fills at most max entries (any pointer may be NULL) and returns
+ * the number of entries. */
+int sw_autotune_entries(int max, int* nc, int* K, int* sites, int* stages, double* us);
 
 /* SplitMix64 stream seed used when psi0 is NULL (level = index into psi0,
  * 0-based): s1 = mix(seed ^ level) + G, result = mix(s1 ^ index) + G, with

@@ -22,7 +22,8 @@ __all__ = [
     "sw_mg_free", "sw_mg_solve", "sw_mg_solve_batch", "sw_debug_maps", "sw_mg_level_info",
     "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_level", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
-    "sw_dslash_schur_noalloc", "sw_debug_cgne_stall", "sw_cg_eo_solve",
+    "sw_dslash_schur_noalloc", "sw_debug_cgne_stall", "sw_cg_eo_solve", "sw_debug_batch_stall",
+    "sw_autotune_entries",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S, SW_OP_DNAIK, SW_OP_ANAIK = 0, 1, 2, 3, 4, 5, 6
@@ -100,6 +101,8 @@ def lib():
             "sw_dslash_schur_noalloc": (_I, [_VP, _D, _VP, _VP]),
             "sw_debug_cgne_stall": (_I, [_VP]),
             "sw_cg_eo_solve": (_I, [_VP, _D, _VP, _VP, _D, _I, _I, ctypes.POINTER(sw_solve_stats)]),
+            "sw_debug_batch_stall": (_I, [_VP, _I]),
+            "sw_autotune_entries": (_I, [_I, _VP, _VP, _VP, _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -400,3 +403,20 @@ def sw_cg_eo_solve(g: _Handle, mass: float, b, x, tol: float, maxiter: int = 100
     d = st.as_dict()
     d["rc"] = rc
     return d
+
+
+def sw_debug_batch_stall(mg: _Handle, nrhs: int = 16) -> int:
+    """Return code of the batched coarsest kernel run with a withheld barrier arrival."""
+    return int(lib().sw_debug_batch_stall(mg.ptr, int(nrhs)))
+
+
+def sw_autotune_entries() -> list:
+    """[(nc, K, coarse sites, stages, us per iteration)] chosen by the autotuner so far."""
+    n = int(lib().sw_autotune_entries(0, None, None, None, None, None))
+    if n <= 0:
+        return []
+    nc, K, sites, st = (np.zeros(n, dtype=np.int32) for _ in range(4))
+    us = np.zeros(n, dtype=np.float64)
+    lib().sw_autotune_entries(n, nc.ctypes.data, K.ctypes.data, sites.ctypes.data,
+                              st.ctypes.data, us.ctypes.data)
+    return [(int(a), int(b), int(c), int(d), float(e)) for a, b, c, d, e in zip(nc, K, sites, st, us)]

@@ -676,4 +676,17 @@ int sw_debug_cgne_stall(sw_mg* mg) {
   });
 }
 
+int sw_debug_batch_stall(sw_mg* mg, int nrhs) {
+  if (!mg) return SW_ERR_ARG;
+  return guarded(mg->ctx, [&] { return mg_batch_stall(mg, nrhs); });
+}
+
+int sw_autotune_entries(int max, int* nc, int* K, int* sites, int* stages, double* us) {
+  try {
+    return mg_autotune_entries(max, nc, K, sites, stages, us);
+  } catch (...) {
+    return SW_ERR_ARG;
+  }
+}
+
 }  // extern "C"

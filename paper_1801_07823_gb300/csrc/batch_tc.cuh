@@ -1,0 +1,721 @@
+// Batched coarsest-level CGNE with the stencil contraction on the tensor cores
+// (tcgen05.mma, TF32 operands, FP32 accumulation in tensor memory), for
+// batched solves of a mixed-precision hierarchy.
+//
+// The iteration is that of batch_cgne.cu (same steps, same stopping rules, one
+// alpha, beta and stopping test per right-hand side); only the stencil
+// products run differently.  For a coarse site X and direction d the product
+// Z v (Z = Z_r + i Z_i the nc x nc block, v = v_r + i v_i the nc x K block of
+// the neighbour's vectors) is one real matrix product
+//     [Z_r; Z_i] (128 x nc)  x  [v_r | v_i] (nc x 2K)
+// whose four quadrants are Z_r v_r, Z_r v_i, Z_i v_r and Z_i v_i; the
+// complex result is formed afterwards:  Re = Z_r v_r - Z_i v_i,
+// Im = Z_r v_i + Z_i v_r.  The five directions of a site accumulate into the
+// same tensor-memory tile (the combination is linear), so a site costs
+// 5 x nc / 8 MMAs of shape M = 128, N = 2K, K = 8 and one read of the tile.
+// Rows 2 nc .. 127 of the stacked block are zero when nc < 64.
+//
+// Operands live in global memory already in the tensor cores' shared-memory
+// layout (K-major, 8-row x 16-byte core matrices, no swizzle): the stacked
+// blocks of A and of A^dag are built once per hierarchy, rounded to TF32, and
+// the kernel writes the right-hand-side tiles of r and p in that layout when it
+// updates them.  One bulk asynchronous copy moves a tile into a pipeline
+// stage; stages complete on mbarrier transaction counts.
+//
+// Roles in a CTA of 256 threads: thread 0 issues the bulk copies, thread 32
+// allocates tensor memory and issues the MMAs (one elected thread), warps 4-7
+// read the accumulator tile (one TMEM lane per thread), combine real and
+// imaginary parts through shared memory, and do the FP64 updates of x, r and
+// p, the TF32 tiles of the next stencil input and the per-right-hand-side
+// norms.  Two accumulator tiles alternate, so the MMAs of one site overlap the
+// epilogue of the previous one.
+//
+// Determinism: every output element is one tensor-core dot product of its own
+// row and column, and norms are summed per site over fixed row groups, per
+// CTA over its sites in order and over the CTAs in order (one CTA per SM), so
+// a right-hand side's scalars do not depend on its batch-mates.
+//
+// Every wait is bounded.  A wait that gives up records SW_ERR_TIMEOUT in the
+// status word; the CTA then stops issuing work, waits (bounded) for the copies
+// and MMAs it has in flight, frees its tensor memory and leaves at the next
+// grid barrier, where every other CTA sees the status and leaves too.
+#pragma once
+#include <string>
+
+#include "sw_internal.h"
+
+namespace swtc {
+
+constexpr long kSpinLimit = 1L << 24;      // grid-barrier polls
+constexpr long kWaitLimit = 1L << 22;      // mbarrier polls
+constexpr int kThreads = 256;
+constexpr int kEpiThreads = 128;           // warps 4..7
+constexpr int kMaxK = 64;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned su32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+static __device__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  for (long k = 0; k < kWaitLimit; ++k)
+    if (mbar_test(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(b))
+      : "memory");
+}
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void epi_sync() {  // named barrier of the epilogue warps
+  asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+}
+__device__ __forceinline__ float to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: start address,
+// byte distance between core matrices adjacent along K (leading) and along
+// M/N (stride), descriptor version 1 (sm_100 family).
+__device__ __forceinline__ unsigned long long smem_desc(unsigned saddr, unsigned kstride,
+                                                        unsigned mstride) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)((kstride >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((mstride >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+// Instruction descriptor of kind::tf32: D in FP32, A and B in TF32, both
+// K-major, shape M x N.
+__host__ __device__ constexpr unsigned idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) |
+         ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(unsigned tmem, unsigned long long ad,
+                                         unsigned long long bd, unsigned id, unsigned acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(b))
+      : "memory");
+}
+// 32 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+// 16 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ int nbr(int X, int d, int E0, int E1) {
+  int X0 = X % E0, X1 = X / E0;
+  if (d == 1) X0 = (X0 + 1 == E0) ? 0 : X0 + 1;
+  if (d == 2) X0 = (X0 == 0) ? E0 - 1 : X0 - 1;
+  if (d == 3) X1 = (X1 + 1 == E1) ? 0 : X1 + 1;
+  if (d == 4) X1 = (X1 == 0) ? E1 - 1 : X1 - 1;
+  return X0 + E0 * X1;
+}
+__device__ __forceinline__ int opp(int d) {
+  return d == 0 ? 0 : (d == 1 ? 2 : (d == 2 ? 1 : (d == 3 ? 4 : 3)));
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle tile with `rows`
+// rows: core matrix (row / 8, k / 4) at (k / 4 * rows / 8 + row / 8) * 128.
+__host__ __device__ __forceinline__ unsigned tile_off(int row, int k, int rows) {
+  return (unsigned)(((k >> 2) * (rows >> 3) + (row >> 3)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// ------------------------------------------------------------ kernel
+struct TcArgs {
+  const float* At;         // [sites][5] stacked forward blocks, 128 x nc TF32 tiles
+  const float* Ad;         // [sites][5] stacked adjoint blocks
+  const double2* const* b; // [K] right-hand sides
+  double2* const* xout;    // [K] solutions
+  double2* X;              // [n][K] FP64 iterates
+  double2* R;
+  double2* P;
+  float* Rt;               // [sites] 2K x nc TF32 tiles of r (stencil input of A^dag)
+  float* Pt;               // [sites] tiles of p (stencil input of A)
+  double* partials;        // [2][K][gridDim.x]
+  unsigned* bar;           // [0] monotone arrival counter
+  int* status;             // [0] timeout / setup failure, [1] non-finite, [2 + r] iterations
+  int nb, E0, E1, maxit;
+  double tol;
+  int stall;               // 1: CTA 0 withholds its first grid-barrier arrival
+};
+
+enum { kInit = 0, kXR = 1, kP = 2 };
+
+template <int NC, int K, int S>
+struct TcCfg {
+  static constexpr int kN = 2 * K;                   // MMA N
+  static constexpr int kATile = 128 * NC * 4;        // bytes of a stacked block
+  static constexpr int kBTile = kN * NC * 4;         // bytes of a right-hand-side tile
+  static constexpr int kStage = kATile + kBTile;
+  static constexpr int kGroups = NC / 8;             // row groups of the norm tree
+  static constexpr int kPairs = K * kGroups;         // (rhs, row group) pairs per site
+  static constexpr int kCols = 2 * kN < 32 ? 32 : 2 * kN;  // TMEM columns (2 tiles)
+  static constexpr int kExch = 128 * 32 * 4;         // exchange buffer, 32 columns
+  static constexpr int kSmem = S * kStage + kExch + 1024;
+  static_assert(NC % 8 == 0 && 2 * NC <= 128, "stacked block must fit M = 128");
+  static_assert(K % 8 == 0 && K <= kMaxK && kN >= 16, "N = 2K in 16 .. 128");
+  static_assert((kCols & (kCols - 1)) == 0 && kCols <= 512, "TMEM columns");
+};
+
+template <int NC, int K, int S>
+struct TcSmem {
+  unsigned long long full[S], empty[S], acc_full[2], acc_empty[2];
+  unsigned tmem;
+  int abort;        // a wait gave up: stop issuing work
+  int epi_go;       // epilogue decision for the current site (uniform over its warps)
+  unsigned issued;  // stages filled so far (producer)
+  unsigned mmaed;   // stages whose MMAs were issued and committed so far
+  double sq[TcCfg<NC, K, S>::kPairs];       // per (rhs, row group) squared norms of a site
+  double cta_sum[K];
+  double red[K][8];
+  double sum[K], rr[K], stop[K], coef[K];
+  int state[K];                              // 0 active, 1 stopped, 2 non-finite
+  int iters[K];
+  int any;
+};
+
+static __device__ bool grid_barrier_tc(unsigned* bar, int* status, unsigned gen) {
+  __shared__ int ok;
+  fence_async_global();  // generic writes of this phase before other CTAs' bulk reads
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned target = gen * gridDim.x;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    volatile unsigned* cnt = bar;
+    long spins = 0;
+    while (*cnt < target) {
+      if (++spins > kSpinLimit) {
+        atomicExch(status, 1);
+        break;
+      }
+      __nanosleep(16);
+    }
+    __threadfence();
+    ok = *((volatile int*)status) == 0;
+  }
+  __syncthreads();
+  return ok;
+}
+
+template <int K>
+__device__ void grid_sums_tc(const double* part, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  for (int r = w; r < K; r += kThreads / 32) {
+    const double* pr = part + r * G;
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = lane + 32 * k < G ? __ldcg(pr + lane + 32 * k) : 0.0;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+    for (int q = lane + 256; q < G; q += 32) s += __ldcg(pr + q);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s;
+  }
+  __syncthreads();
+}
+
+template <typename Sm>
+__device__ __forceinline__ bool aborted(const Sm& sm) {
+  return *((const volatile int*)&sm.abort) != 0;
+}
+
+// Counters of the pipeline that persist across phases.
+struct Pipe {
+  unsigned q;  // stages used so far (buffer q % S, parity (q / S) & 1)
+  unsigned a;  // accumulator tiles used so far (tile a & 1, parity (a >> 1) & 1)
+};
+
+// One stencil application over this CTA's sites fused with the update of the
+// phase; leaves this CTA's per-right-hand-side norm sums in sm.cta_sum.
+template <int NC, int K, int S, int MODE>
+__device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
+                         TcSmem<NC, K, S>& sm, Pipe& pp) {
+  using C = TcCfg<NC, K, S>;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int nsites = a.E0 * a.E1;
+  const int nmine = cta < nsites ? (nsites - 1 - cta) / G + 1 : 0;
+  const int nitems = nmine * 5;
+  const float* Ablk = MODE == kXR ? a.At : a.Ad;
+  const float* Vt = MODE == kXR ? a.Pt : a.Rt;
+  if (t < K) sm.cta_sum[t] = 0.0;
+
+  if (t == 0) {
+    // ---------------- producer: one (site, direction) pair per stage
+    fence_async_global();
+    for (int it = 0; it < nitems && !aborted(sm); ++it) {
+      const unsigned q = pp.q + it;
+      const int s = q % S;
+      if (q >= (unsigned)S && !mbar_wait(&sm.empty[s], ((q / S) - 1) & 1u)) {
+        sm.abort = 1;
+        atomicExch(a.status, 1);
+        break;
+      }
+      const int m = it / 5, d = it - 5 * m;
+      const int X = cta + G * m;
+      const int nb = nbr(X, d, a.E0, a.E1);
+      unsigned char* buf = stages + (size_t)s * C::kStage;
+      mbar_expect(&sm.full[s], (unsigned)C::kStage);
+      bulk_load(buf, Ablk + ((size_t)X * 5 + d) * (C::kATile / 4), C::kATile, &sm.full[s]);
+      bulk_load(buf + C::kATile, Vt + (size_t)nb * (C::kBTile / 4), C::kBTile, &sm.full[s]);
+      sm.issued = q + 1;
+    }
+  } else if (t == 32) {
+    // ---------------- MMA issuer
+    constexpr unsigned id = idesc_tf32(128, C::kN);
+    for (int it = 0; it < nitems && !aborted(sm); ++it) {
+      const unsigned q = pp.q + it;
+      const int s = q % S;
+      const int m = it / 5, d = it - 5 * m;
+      const unsigned at = pp.a + m;
+      const int tile = at & 1;
+      if (d == 0 && at >= 2 && !mbar_wait(&sm.acc_empty[tile], ((at >> 1) - 1) & 1u)) {
+        sm.abort = 1;
+        atomicExch(a.status, 1);
+        break;
+      }
+      if (!mbar_wait(&sm.full[s], (q / S) & 1u)) {
+        sm.abort = 1;
+        atomicExch(a.status, 1);
+        break;
+      }
+      tc_fence_after();
+      const unsigned base = su32(stages + (size_t)s * C::kStage);
+      const unsigned tmem = sm.tmem + (unsigned)(tile * C::kN);
+#pragma unroll
+      for (int ks = 0; ks < NC / 8; ++ks) {
+        const unsigned long long ad = smem_desc(base + ks * 2 * 2048, 2048, 128);
+        const unsigned long long bd =
+            smem_desc(base + C::kATile + ks * 2 * (C::kN / 8) * 128, (C::kN / 8) * 128, 128);
+        mma_tf32(tmem, ad, bd, id, (d > 0 || ks > 0) ? 1u : 0u);
+      }
+      mma_commit(&sm.empty[s]);                     // stage free once these MMAs are done
+      if (d == 4) mma_commit(&sm.acc_full[tile]);  // site's tile complete
+      sm.mmaed = q + 1;
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue: one TMEM lane (stacked row) per thread
+    const int e = t - 128;                 // 0 .. 127
+    const int lrow = e;                    // TMEM lane = row of the stacked product
+    for (int m = 0; m < nmine; ++m) {
+      const unsigned at = pp.a + m;
+      const int tile = at & 1;
+      // one thread waits for the tile; the decision is shared so that every
+      // epilogue thread takes the same branch at the named barriers below
+      if (e == 0) {
+        int go = !aborted(sm) && mbar_wait(&sm.acc_full[tile], (at >> 1) & 1u);
+        if (!go && !aborted(sm)) {
+          sm.abort = 1;
+          atomicExch(a.status, 1);
+        }
+        sm.epi_go = go;
+      }
+      epi_sync();
+      if (!sm.epi_go) break;
+      tc_fence_after();
+      const int X = cta + G * m;
+      // the combination of group g needs columns [16 g, 16 g + 16) and
+      // [K + 16 g, K + 16 g + 16) of rows i and i + NC
+      for (int g = 0; g < K / 16 || (K < 16 && g == 0); ++g) {
+        const int c0 = K < 16 ? 0 : 16 * g;       // K = 8: both halves in one 16-column load
+        const unsigned lane_base = ((unsigned)(32 * (warp - 4))) << 16;
+        epi_sync();  // previous group's readers are done with exch
+        {
+          float w[32];
+          if (K < 16) {
+            tmem_ld16(sm.tmem + lane_base + tile * C::kN, w);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) exch[lrow * 32 + ((c + lrow) & 31)] = w[c];
+          } else {
+            tmem_ld32(sm.tmem + lane_base + tile * C::kN + (c0 & ~31), w);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) exch[lrow * 32 + ((c + lrow) & 31)] = w[(c0 & 31) + c];
+            tmem_ld32(sm.tmem + lane_base + tile * C::kN + ((K + c0) & ~31), w);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              exch[lrow * 32 + ((16 + c + lrow) & 31)] = w[((K + c0) & 31) + c];
+          }
+        }
+        epi_sync();
+        // combine: columns 0..15 hold Re-part products of rhs c0 + c (K = 8: 0..7),
+        // columns 16..31 those of the imaginary parts (K = 8: columns 8..15)
+        const int kg = K < 16 ? K : 16;
+        const int ioff = K < 16 ? K : 16;  // column of the first imaginary-part product
+        for (int pidx = e; pidx < kg * C::kGroups; pidx += kEpiThreads) {
+          const int r = c0 + pidx % kg, grp = pidx / kg;
+          const int cr = pidx % kg;
+          double q2 = 0.0;
+          for (int i = grp * 8; i < grp * 8 + 8; ++i) {
+            auto E = [&](int row, int col) { return exch[row * 32 + ((col + row) & 31)]; };
+            const float re = E(i, cr) - E(i + NC, ioff + cr);
+            const float im = E(i, ioff + cr) + E(i + NC, cr);
+            const size_t el = ((size_t)X * NC + i) * K + r;
+            float* vt = (MODE == kXR ? a.Rt : a.Pt) + (size_t)X * (C::kBTile / 4);
+            if (MODE == kInit) {
+              const double2 pv = make_double2((double)re, (double)im);
+              a.P[el] = pv;
+              vt[tile_off(r, i, C::kN) / 4] = to_tf32(re);
+              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32(im);
+              q2 += fma(pv.x, pv.x, pv.y * pv.y);
+            } else if (MODE == kXR) {
+              double2 xv = __ldcg(a.X + el), rv = __ldcg(a.R + el);
+              if (sm.state[r] == 0) {
+                const double al = sm.coef[r];
+                const double2 pv = __ldcg(a.P + el);
+                xv.x = fma(al, pv.x, xv.x);
+                xv.y = fma(al, pv.y, xv.y);
+                rv.x = fma(-al, (double)re, rv.x);
+                rv.y = fma(-al, (double)im, rv.y);
+                a.X[el] = xv;
+                a.R[el] = rv;
+                q2 += fma(rv.x, rv.x, rv.y * rv.y);
+              }
+              vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)rv.x);
+              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)rv.y);
+            } else {
+              double2 pv = __ldcg(a.P + el);
+              if (sm.state[r] == 0) {
+                const double be = sm.coef[r];
+                pv.x = fma(be, pv.x, (double)re);
+                pv.y = fma(be, pv.y, (double)im);
+                a.P[el] = pv;
+                q2 += fma(pv.x, pv.x, pv.y * pv.y);
+              }
+              vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)pv.x);
+              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)pv.y);
+            }
+          }
+          sm.sq[r * C::kGroups + grp] = q2;
+        }
+      }
+      // tile read: hand it back to the MMA issuer
+      tc_fence_before();
+      epi_sync();
+      if (e == 0) mbar_arrive(&sm.acc_empty[tile]);
+      // site sums over row groups in order, then the CTA's running sum
+      if (e < K) {
+        double sv = 0.0;
+        for (int grp = 0; grp < C::kGroups; ++grp) sv += sm.sq[e * C::kGroups + grp];
+        sm.cta_sum[e] += sv;
+      }
+    }
+  }
+  pp.q += (unsigned)nitems;
+  pp.a += (unsigned)nmine;
+  __syncthreads();
+}
+
+// After a wait gave up: wait (bounded) for every copy and MMA this CTA may
+// still have in flight (the last fill of each stage and the MMAs issued on
+// it), so that none is outstanding when the tensor memory is freed.
+template <int NC, int K, int S>
+__device__ void tc_drain(TcSmem<NC, K, S>& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned is = sm.issued, mm = sm.mmaed;
+    for (unsigned q = is >= (unsigned)S ? is - S : 0u; q < is; ++q)
+      mbar_wait(&sm.full[q % S], (q / S) & 1u);
+    for (unsigned q = mm >= (unsigned)S ? mm - S : 0u; q < mm; ++q)
+      mbar_wait(&sm.empty[q % S], (q / S) & 1u);
+  }
+  __syncthreads();
+}
+
+template <int NC, int K, int S>
+__global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
+  using C = TcCfg<NC, K, S>;
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  __shared__ TcSmem<NC, K, S> sm;
+  unsigned char* stages =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<size_t>(dyn) + 1023) & ~(size_t)1023);
+  float* exch = reinterpret_cast<float*>(stages + (size_t)S * C::kStage);
+  const int t = threadIdx.x;
+  const long n = (long)a.E0 * a.E1 * NC;
+  const long tid = (long)blockIdx.x * blockDim.x + t;
+  const long nthr = (long)gridDim.x * blockDim.x;
+  Pipe pp{0u, 0u};
+  unsigned gen = 0;
+
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&sm.acc_full[k], 1);
+      mbar_init(&sm.acc_empty[k], 1);
+    }
+    sm.abort = 0;
+    sm.issued = sm.mmaed = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_shared();
+    const size_t gl = (size_t)a.At | (size_t)a.Ad | (size_t)a.Rt | (size_t)a.Pt;
+    if (((su32(stages) & 1023u) | (unsigned)(gl & 127)) != 0) atomicExch(a.status, 1);
+  }
+  if ((t >> 5) == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&sm.tmem)),
+                 "r"(C::kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  // gather: X = 0, R = b, Rt = tf32(b); then ||r||^2 per right-hand side, each
+  // summed over this thread's dofs in the same order for every width K
+  for (long dof = tid; dof < n; dof += nthr) {
+    const int X = (int)(dof / NC), i = (int)(dof - (long)X * NC);
+    float* vt = a.Rt + (size_t)X * (C::kBTile / 4);
+    for (int r = 0; r < K; ++r) {
+      const double2 v = r < a.nb ? a.b[r][dof] : make_double2(0.0, 0.0);
+      a.X[dof * K + r] = make_double2(0.0, 0.0);
+      a.R[dof * K + r] = v;
+      vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)v.x);
+      vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)v.y);
+    }
+  }
+  int ph = 0;
+  {
+    const int lane = t & 31, w = t >> 5;
+    for (int r = 0; r < K; ++r) {
+      double s = 0.0;
+      if (r < a.nb)
+        for (long dof = tid; dof < n; dof += nthr) {
+          const double2 v = a.b[r][dof];
+          s = fma(v.x, v.x, fma(v.y, v.y, s));
+        }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sm.red[r][w] = s;
+    }
+    __syncthreads();
+    if (t < K) {
+      double s = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) s += sm.red[t][q];
+      a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = s;
+    }
+  }
+  bool go = true;
+  if (a.stall && blockIdx.x == 0) go = false;  // withheld arrival: the others time out
+  if (go) go = grid_barrier_tc(a.bar, a.status, ++gen);
+  if (go) {
+    grid_sums_tc<K>(a.partials + ph * K * gridDim.x, sm.sum);
+    if (t < K) {
+      const double rr0 = sm.sum[t];
+      sm.rr[t] = rr0;
+      sm.stop[t] = a.tol * sqrt(rr0);
+      sm.iters[t] = 0;
+      sm.state[t] = !isfinite(rr0) ? 2 : ((a.maxit <= 0 || !(sqrt(rr0) > sm.stop[t])) ? 1 : 0);
+    }
+    __syncthreads();
+    ph ^= 1;
+    // p = A^dag r, ||p||^2
+    tc_phase<NC, K, S, kInit>(a, stages, exch, sm, pp);
+    if (t < K) a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = sm.cta_sum[t];
+    go = !aborted(sm) && grid_barrier_tc(a.bar, a.status, ++gen);
+  }
+  if (go) {
+    grid_sums_tc<K>(a.partials + ph * K * gridDim.x, sm.sum);
+    if (t < K) sm.coef[t] = sm.rr[t] / sm.sum[t];  // alpha
+    if (t == 0) {
+      int any = 0;
+      for (int r = 0; r < K; ++r) any |= sm.state[r] == 0;
+      sm.any = any;
+    }
+    __syncthreads();
+    ph ^= 1;
+    while (sm.any) {
+      tc_phase<NC, K, S, kXR>(a, stages, exch, sm, pp);  // w = A p; x += alpha p; r -= alpha w
+      if (t < K) a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = sm.cta_sum[t];
+      if (aborted(sm) || !grid_barrier_tc(a.bar, a.status, ++gen)) {
+        go = false;
+        break;
+      }
+      grid_sums_tc<K>(a.partials + ph * K * gridDim.x, sm.sum);
+      if (t < K && sm.state[t] == 0) {
+        const double rr_new = sm.sum[t];
+        const int k = ++sm.iters[t];
+        if (!isfinite(rr_new))
+          sm.state[t] = 2;
+        else if (!(k < a.maxit && sqrt(rr_new) > sm.stop[t]))
+          sm.state[t] = 1;
+        sm.coef[t] = rr_new / sm.rr[t];  // beta
+        sm.rr[t] = rr_new;
+      }
+      __syncthreads();
+      if (t == 0) {
+        int any = 0;
+        for (int r = 0; r < K; ++r) any |= sm.state[r] == 0;
+        sm.any = any;
+      }
+      __syncthreads();
+      ph ^= 1;
+      if (!sm.any) break;
+      tc_phase<NC, K, S, kP>(a, stages, exch, sm, pp);  // p = A^dag r + beta p
+      if (t < K) a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = sm.cta_sum[t];
+      if (aborted(sm) || !grid_barrier_tc(a.bar, a.status, ++gen)) {
+        go = false;
+        break;
+      }
+      grid_sums_tc<K>(a.partials + ph * K * gridDim.x, sm.sum);
+      if (t < K && sm.state[t] == 0) sm.coef[t] = sm.rr[t] / sm.sum[t];  // alpha
+      __syncthreads();
+      ph ^= 1;
+    }
+  }
+  if (!go) {
+    if (aborted(sm)) atomicExch(a.status, 1);
+    tc_drain<NC, K, S>(sm);
+  }
+  // every MMA of this CTA has completed here (the epilogue waited for each
+  // site's tile, or the drain above waited for the stages); free the columns
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((t >> 5) == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem),
+                 "r"(C::kCols)
+                 : "memory");
+  if (!go) return;
+  for (long dof = tid; dof < n; dof += nthr)
+    for (int r = 0; r < a.nb; ++r) a.xout[r][dof] = __ldcg(a.X + dof * K + r);
+  if (blockIdx.x == 0 && t < K) {
+    if (sm.state[t] == 2) atomicExch(a.status + 1, 1);
+    a.status[2 + t] = sm.iters[t];
+  }
+}
+
+template <int NC, int K, int S>
+void launch_tc_t(const TcArgs& args, int grid, cudaStream_t s) {
+  using C = TcCfg<NC, K, S>;
+  TcArgs a = args;
+  void* params[] = {&a};
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne_tc<NC, K, S>, dim3(grid),
+                                      dim3(kThreads), params, C::kSmem, s));
+  sw_count_launch();
+}
+
+template <int NC, int K, int S>
+bool prepare_t(int device, int& grid) {
+  using C = TcCfg<NC, K, S>;
+  int occ = 0, sms = 0, coop = 0;
+  SW_CUDA(cudaFuncSetAttribute((const void*)k_cgne_tc<NC, K, S>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+  SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne_tc<NC, K, S>, kThreads,
+                                                        C::kSmem));
+  SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+  if (!coop || occ < 1) return false;
+  grid = sms;
+  return true;
+}
+
+// Launches the kernel of one (NC, K, S) on the first call per device after
+// checking that it fits; false if it cannot run cooperatively.
+template <int NC, int K, int S>
+bool run_t(const TcArgs& a, int device, cudaStream_t s) {
+  static int grids[64] = {0};
+  int& grid = grids[device & 63];
+  if (!grid && !prepare_t<NC, K, S>(device, grid)) return false;
+  launch_tc_t<NC, K, S>(a, grid, s);
+  return true;
+}
+
+// Dispatch over the widths and depths compiled for one NC (one translation
+// unit per NC, so that they compile in parallel).
+template <int NC>
+bool run_nc(const TcArgs& a, int K, int S, int device, cudaStream_t s) {
+  if (K == 8 && S == 2) return run_t<NC, 8, 2>(a, device, s);
+  if (K == 8 && S == 4) return run_t<NC, 8, 4>(a, device, s);
+  if (K == 16 && S == 2) return run_t<NC, 16, 2>(a, device, s);
+  if (K == 16 && S == 4) return run_t<NC, 16, 4>(a, device, s);
+  if (K == 32 && S == 2) return run_t<NC, 32, 2>(a, device, s);
+  if (K == 32 && S == 3) return run_t<NC, 32, 3>(a, device, s);
+  if (K == 64 && S == 2) return run_t<NC, 64, 2>(a, device, s);
+  if (K == 64 && S == 3) return run_t<NC, 64, 3>(a, device, s);
+  return false;
+}
+
+bool run_nc16(const TcArgs& a, int K, int S, int device, cudaStream_t s);
+bool run_nc24(const TcArgs& a, int K, int S, int device, cudaStream_t s);
+bool run_nc64(const TcArgs& a, int K, int S, int device, cudaStream_t s);
+
+}  // namespace swtc

@@ -22,7 +22,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "sw_internal.h"
 #include "sw_mg.h"
@@ -250,20 +252,85 @@ constexpr int kIterBatch = 8;
 // while waiting at a grid barrier for their own remaining CTAs.
 static std::mutex g_persistent_mutex;
 
+// Autotuner records, keyed by (device, nc, batch width, coarse sites): for the
+// batched tensor-core kernel the pipeline depth, for the single-right-hand-side
+// FP64 kernel (width 1) its variant (0: four-FMA, 1: three-FMA products).
+struct TuneRec {
+  int stages;
+  double us_per_iter;
+};
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, int, int, int>, TuneRec> g_tune;
+
+// Variant of the FP64 coarsest CGNE for this level, chosen on first use per
+// (device, nc, sites) by timing each for a few iterations on the call's own
+// data (the real solve then starts from scratch).
+static int cgne64_variant(sw_mg* mg, MgLevel& L, const double2* b, double2* x) {
+  sw_ctx* c = mg->ctx;
+  const auto key = std::make_tuple(c->device, L.nc, 1, L.E0 * L.E1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second.stages;
+  }
+  constexpr int kTuneIters = 8, kReps = 2;
+  cudaEvent_t e0, e1;
+  SW_CUDA(cudaEventCreate(&e0));
+  SW_CUDA(cudaEventCreate(&e1));
+  TuneRec best{0, 1e30};
+  for (int v = 0; v < 2; ++v) {
+    float tot = 0.f;
+    for (int rep = 0; rep <= kReps; ++rep) {  // rep 0 is a warm-up
+      SW_CUDA(cudaEventRecord(e0, c->stream));
+      bool ran = launch_cgne64(CoarseGeom{L.E0, L.E1, L.nc}, v, L.Y, L.Ys, b, x, L.gr, L.cp,
+                               L.c4, c->partials, c->bar, c->cgstat, kTuneIters, 0.0, c->device,
+                               c->stream);
+      SW_CUDA(cudaEventRecord(e1, c->stream));
+      SW_CUDA(cudaEventSynchronize(e1));
+      SW_REQUIRE(ran, SW_ERR_ARG, "FP64 coarsest CGNE has no variant for this shape");
+      int st[3];
+      SW_CUDA(cudaMemcpy(st, c->cgstat, sizeof(st), cudaMemcpyDeviceToHost));
+      SW_REQUIRE(st[1] == 0, SW_ERR_TIMEOUT, "coarsest CGNE: a grid barrier wait gave up");
+      float ms = 0.f;
+      SW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;
+    }
+    const double us = 1e3 * tot / kReps / kTuneIters;
+    if (us < best.us_per_iter) best = TuneRec{v, us};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune[key] = best;
+  return best.stages;
+}
+
 static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
   sw_ctx* c = mg->ctx;
   MgLevel& L = mg->lev[l];
   long n = level_len(mg, l);
   if (mg->persistent_cgne) {
     std::lock_guard<std::mutex> lock(g_persistent_mutex);  // held until the kernel has finished
-    int tk = timing_begin(c, kCatCgne);
-    bool df = mg->mixed && L.Ydf;
-    bool ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, df ? (const void*)L.Ydf
-                                                                      : (const void*)L.Y,
-                                      df ? 1 : 0, b, x, L.gr, L.cp, L.cdf,
-                                      L.cdf ? L.cdf + L.ndof : nullptr,
-                                      c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
-                                      mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
+    int tk = -1;
+    const char* dfenv = std::getenv("SW_COARSEST_DF64");
+    bool df = mg->mixed && L.Ydf && (!(L.Ys && L.c4) || (dfenv && dfenv[0] == '1'));
+    bool ran;
+    if (!df && L.Ys && L.c4) {
+      const int v = cgne64_variant(mg, L, b, x);
+      tk = timing_begin(c, kCatCgne);  // the bracket covers the solve, not the tuning
+      ran = launch_cgne64(CoarseGeom{L.E0, L.E1, L.nc}, v, L.Y, L.Ys, b, x, L.gr, L.cp, L.c4,
+                          c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
+                          mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
+    }
+    else {
+      tk = timing_begin(c, kCatCgne);
+      ran = launch_cgne_persistent(CoarseGeom{L.E0, L.E1, L.nc}, df ? (const void*)L.Ydf
+                                                                   : (const void*)L.Y,
+                                   df ? 1 : 0, b, x, L.gr, L.cp, L.cdf,
+                                   L.cdf ? L.cdf + L.ndof : nullptr,
+                                   c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
+                                   mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
+    }
     timing_end(c, tk);
     if (ran) {
       SW_CUDA(cudaMemcpyAsync(c->h_ctl, c->cgstat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
@@ -455,6 +522,12 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed) {
       double2* T = tmp.get((long)L.E0 * L.E1 * 5 * L.nc * 2 * nv);
       launch_build_Y_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, nv, L.Y, L.P, T, C.Y, s);
     }
+    if (l + 2 == mg->nlev && !mg->fine_D && cgne64_supported(C.nc)) {
+      // coarsest level: the sum plane and vector forms of its FP64 CGNE
+      C.Ys = (double*)mg_alloc(mg, (ysz + 1) / 2);
+      launch_sum_planes(C.Y, C.Ys, ysz, s);
+      C.c4 = (double*)mg_alloc(mg, 4 * C.ndof);
+    }
     if (mg->mixed) {
       CoarseGeom cg{C.E0, C.E1, C.nc};
       if (l + 2 < mg->nlev) {  // intermediate level: scaled FP16 copy
@@ -579,9 +652,10 @@ using Set = std::vector<int>;
 
 inline int page(int r) { return (r + 1) * kSlotPage; }
 
-// Reads the whole slot array back once (every page) after the queued reductions.
-const double2* slots_read_all(sw_ctx* c) {
-  SW_CUDA(cudaMemcpyAsync(c->h_slots, c->slots, kNumSlots * sizeof(double2),
+// Reads the slot pages of the batch (page 0 and those of its nb right-hand
+// sides) back once after the queued reductions.
+const double2* slots_read_all(sw_ctx* c, int nb) {
+  SW_CUDA(cudaMemcpyAsync(c->h_slots, c->slots, (size_t)kSlotPage * (nb + 1) * sizeof(double2),
                           cudaMemcpyDeviceToHost, c->stream));
   SW_CUDA(cudaStreamSynchronize(c->stream));
   if (!c->pending.empty()) timing_harvest(c);
@@ -691,7 +765,7 @@ SetResult fgcr_b(sw_mg* mg, int l, const Set& set, const std::vector<const doubl
       if (!done[r]) act.push_back(r);
     if (act.empty()) break;
     for (int r : act) blas_norm2(c, mg->batch.lv[l][r].gr, n, slot_base(l) + page(r));
-    const double2* hs = slots_read_all(c);
+    const double2* hs = slots_read_all(c, nb);
     Set cand, go;
     for (int r : act) {
       double rn = std::sqrt(hs[slot_base(l) + page(r)].x);
@@ -716,7 +790,7 @@ SetResult fgcr_b(sw_mg* mg, int l, const Set& set, const std::vector<const doubl
         blas_sub(c, W.gtmp, b[r], W.gtmp, n);
         blas_norm2(c, W.gtmp, n, slot_base(l) + page(r) + 1);
       }
-      const double2* hs2 = slots_read_all(c);
+      const double2* hs2 = slots_read_all(c, nb);
       for (int r : cand) {
         double rt = std::sqrt(hs2[slot_base(l) + page(r) + 1].x);
         check_norm(rt, "batched GCR true residual");
@@ -775,43 +849,114 @@ SetResult fgcr_b(sw_mg* mg, int l, const Set& set, const std::vector<const doubl
   return res;
 }
 
-void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
+// ---------------------------------------------------------------- autotuner
+// Pipeline depth of the tensor-core batched CGNE, chosen on first use per
+// (device, nc, width, coarse sites) by timing each candidate for a few
+// iterations on the call's own data (the real solve then starts from scratch).
+
+int tc_stages(sw_mg* mg, const MgLevel& L, int nb, double2* const* bptr, double2* const* xptr) {
+  sw_ctx* c = mg->ctx;
+  BatchWs& B = mg->batch;
+  const int K = tc_width(nb);
+  const auto key = std::make_tuple(c->device, L.nc, K, L.E0 * L.E1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second.stages;
+  }
+  int opts[8];
+  const int nopt = tc_stage_options(L.nc, K, opts);
+  SW_REQUIRE(nopt > 0, SW_ERR_ARG, "no tensor-core tiling fits shared memory");
+  constexpr int kTuneIters = 6, kReps = 2;
+  cudaEvent_t e0, e1;
+  SW_CUDA(cudaEventCreate(&e0));
+  SW_CUDA(cudaEventCreate(&e1));
+  TuneRec best{opts[0], 1e30};
+  for (int k = 0; k < nopt; ++k) {
+    float tot = 0.f;
+    for (int rep = 0; rep <= kReps; ++rep) {  // rep 0 is a warm-up
+      SW_CUDA(cudaEventRecord(e0, c->stream));
+      bool ran = launch_cgne_tc(CoarseGeom{L.E0, L.E1, L.nc}, opts[k], B.At, B.Ad, nb, bptr,
+                                xptr, B.X, B.R, B.P, B.Rt, B.Pt, B.partials, B.bar, B.status,
+                                kTuneIters, 0.0, c->device, c->stream, 0);
+      SW_CUDA(cudaEventRecord(e1, c->stream));
+      SW_CUDA(cudaEventSynchronize(e1));
+      SW_REQUIRE(ran, SW_ERR_ARG, "tensor-core batched CGNE has no variant for this shape");
+      int st0 = 0;
+      SW_CUDA(cudaMemcpy(&st0, B.status, sizeof(int), cudaMemcpyDeviceToHost));
+      SW_REQUIRE(st0 == 0, SW_ERR_TIMEOUT, "batched coarsest CGNE: a wait gave up while tuning");
+      float ms = 0.f;
+      SW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;
+    }
+    const double us = 1e3 * tot / kReps / kTuneIters;
+    if (us < best.us_per_iter) best = TuneRec{opts[k], us};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune[key] = best;
+  return best.stages;
+}
+
+void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc, int stall = 0) {
   if (set.empty()) return;
   sw_ctx* c = mg->ctx;
   MgLevel& L = mg->lev[l];
   BatchWs& B = mg->batch;
-  int nb = (int)set.size();
-  double2* hp[32] = {nullptr};
+  const int nb = (int)set.size();
+  const bool tc = tc_supported(L.nc) && !B.Yf;
+  double2* hp[2 * kMaxBatch] = {nullptr};
   for (int i = 0; i < nb; ++i) {
     hp[i] = B.lv[l][set[i]].rhs;
-    hp[16 + i] = B.lv[l][set[i]].sol;
+    hp[kMaxBatch + i] = B.lv[l][set[i]].sol;
   }
   SW_CUDA(cudaMemcpyAsync(B.dptr, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));
   SW_CUDA(cudaStreamSynchronize(c->stream));  // hp is a host stack array
   std::lock_guard<std::mutex> lock(g_persistent_mutex);
-  int tk = timing_begin(c, kCatCgne);
-  bool ran = launch_cgne_batch(CoarseGeom{L.E0, L.E1, L.nc}, B.Yf, B.Yd, nb, B.dptr,
-                               B.dptr + 16, B.X, B.R, B.P, B.Rf, B.Pf, B.partials, B.bar,
-                               B.status, mg->p.coarsest_maxiter, mg->p.coarsest_tol, c->device,
-                               c->stream);
-  timing_end(c, tk);
-  if (!ran)
-    throw SwError{SW_ERR_ARG, "no batched coarsest solver for nc = " + std::to_string(L.nc)};
-  int hst[18];
-  SW_CUDA(cudaMemcpyAsync(hst, B.status, sizeof(hst), cudaMemcpyDeviceToHost, c->stream));
-  SW_CUDA(cudaStreamSynchronize(c->stream));
-  if (!c->pending.empty()) timing_harvest(c);
-  if (hst[0])
-    throw SwError{SW_ERR_TIMEOUT,
-                  "batched coarsest CGNE: a wait gave up or a buffer was misaligned"};
-  if (hst[1]) throw SwError{SW_ERR_NAN, "non-finite norm in batched CGNE"};
-  int kernel_it = 0;  // the launch runs as many iterations as its slowest right-hand side
-  for (int i = 0; i < nb; ++i) {
-    bc.coarse_it[set[i]] += hst[2 + i];
-    bc.coarse_solves[set[i]]++;
-    kernel_it = std::max(kernel_it, hst[2 + i]);
+  std::vector<int> its(nb, 0);
+  // the CUDA-core FP32 kernel (SW_BATCH_FP32=1) takes at most 16 at a time
+  const int chunk = tc ? kMaxBatch : 16;
+  for (int i0 = 0; i0 < nb; i0 += chunk) {
+    const int m = std::min(chunk, nb - i0);
+    bool ran;
+    int tk;
+    if (tc) {
+      const int S = tc_stages(mg, L, m, B.dptr + i0, B.dptr + kMaxBatch + i0);
+      tk = timing_begin(c, kCatCgne);
+      ran = launch_cgne_tc(CoarseGeom{L.E0, L.E1, L.nc}, S, B.At, B.Ad, m, B.dptr + i0,
+                           B.dptr + kMaxBatch + i0, B.X, B.R, B.P, B.Rt, B.Pt, B.partials,
+                           B.bar, B.status, mg->p.coarsest_maxiter, mg->p.coarsest_tol,
+                           c->device, c->stream, stall);
+    } else {
+      tk = timing_begin(c, kCatCgne);
+      ran = launch_cgne_batch(CoarseGeom{L.E0, L.E1, L.nc}, B.Yf, B.Yd, m, B.dptr + i0,
+                              B.dptr + kMaxBatch + i0, B.X, B.R, B.P, B.Rf, B.Pf, B.partials,
+                              B.bar, B.status, mg->p.coarsest_maxiter, mg->p.coarsest_tol,
+                              c->device, c->stream);
+    }
+    timing_end(c, tk);
+    if (!ran)
+      throw SwError{SW_ERR_ARG, "no batched coarsest solver for nc = " + std::to_string(L.nc)};
+    int hst[2 + kMaxBatch];
+    SW_CUDA(cudaMemcpyAsync(hst, B.status, sizeof(hst), cudaMemcpyDeviceToHost, c->stream));
+    SW_CUDA(cudaStreamSynchronize(c->stream));
+    if (!c->pending.empty()) timing_harvest(c);
+    if (hst[0])
+      throw SwError{SW_ERR_TIMEOUT,
+                    "batched coarsest CGNE: a wait gave up or a buffer was misaligned"};
+    if (hst[1]) throw SwError{SW_ERR_NAN, "non-finite norm in batched CGNE"};
+    int kernel_it = 0;  // the launch runs as many iterations as its slowest right-hand side
+    for (int i = 0; i < m; ++i) {
+      its[i0 + i] = hst[2 + i];
+      kernel_it = std::max(kernel_it, hst[2 + i]);
+    }
+    if (c->timing) c->t_count[kCatCgne + 1] += kernel_it;
   }
-  if (c->timing) c->t_count[kCatCgne + 1] += kernel_it;
+  for (int i = 0; i < nb; ++i) {
+    bc.coarse_it[set[i]] += its[i];
+    bc.coarse_solves[set[i]]++;
+  }
 }
 
 void solve_level_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
@@ -823,7 +968,7 @@ void solve_level_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
   long n = level_len(mg, l);
   int nb = mg->batch.nb;
   for (int r : set) blas_norm2(c, mg->batch.lv[l][r].rhs, n, slot_base(l) + page(r) + 5);
-  const double2* hs = slots_read_all(c);
+  const double2* hs = slots_read_all(c, nb);
   std::vector<double> tol(nb, 0.0);
   std::vector<const double2*> b(nb, nullptr);
   std::vector<double2*> x(nb, nullptr);
@@ -842,54 +987,78 @@ void solve_level_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc) {
   }
 }
 
-void batch_alloc(sw_mg* mg) {
+// Per-right-hand-side work vectors for nb right-hand sides (grown on demand)
+// and, on the first call, the arrays all of them share.
+void batch_alloc(sw_mg* mg, int nb) {
   BatchWs& B = mg->batch;
-  if (B.nb) return;
+  sw_ctx* c = mg->ctx;
   long N = mg->g->N;
-  B.lv.assign(mg->nlev, std::vector<LevelWs>(kMaxBatch));
-  for (int l = 0; l < mg->nlev; ++l) {
-    long n = level_len(mg, l);
-    bool last = l == mg->nlev - 1;
-    int nbas = last ? 0 : (l == 0 ? mg->p.outer_restart : mg->p.inter_restart);
-    for (int r = 0; r < kMaxBatch; ++r) {
-      LevelWs& W = B.lv[l][r];
-      W.rhs = mg_alloc(mg, n);
-      W.sol = mg_alloc(mg, n);
-      if (last) continue;
-      W.gr = mg_alloc(mg, n);
-      W.gtmp = mg_alloc(mg, n);
-      W.gp.assign(nbas, nullptr);
-      W.gq.assign(nbas, nullptr);
-      for (int k = 0; k < nbas; ++k) {
-        W.gp[k] = mg_alloc(mg, n);
-        W.gq[k] = mg_alloc(mg, n);
+  if (B.lv.empty()) B.lv.assign(mg->nlev, std::vector<LevelWs>());
+  if (nb > B.nb) {
+    const int cap = std::min(kMaxBatch, std::max(nb, 2 * B.nb));
+    for (int l = 0; l < mg->nlev; ++l) {
+      long n = level_len(mg, l);
+      bool last = l == mg->nlev - 1;
+      int nbas = last ? 0 : (l == 0 ? mg->p.outer_restart : mg->p.inter_restart);
+      B.lv[l].resize(cap);
+      for (int r = B.nb; r < cap; ++r) {
+        LevelWs& W = B.lv[l][r];
+        W.rhs = mg_alloc(mg, n);
+        W.sol = mg_alloc(mg, n);
+        if (last) continue;
+        W.gr = mg_alloc(mg, n);
+        W.gtmp = mg_alloc(mg, n);
+        W.gp.assign(nbas, nullptr);
+        W.gq.assign(nbas, nullptr);
+        for (int k = 0; k < nbas; ++k) {
+          W.gp[k] = mg_alloc(mg, n);
+          W.gq[k] = mg_alloc(mg, n);
+        }
+        W.kx1 = mg_alloc(mg, n); W.kr1 = mg_alloc(mg, n); W.kq = mg_alloc(mg, n);
+        W.ke = mg_alloc(mg, n); W.kr2 = mg_alloc(mg, n); W.kx3 = mg_alloc(mg, n);
       }
-      W.kx1 = mg_alloc(mg, n); W.kr1 = mg_alloc(mg, n); W.kq = mg_alloc(mg, n);
-      W.ke = mg_alloc(mg, n); W.kr2 = mg_alloc(mg, n); W.kx3 = mg_alloc(mg, n);
     }
+    B.nb = cap;
   }
+  if (B.shared) return;
   MgLevel& C = mg->lev[mg->nlev - 1];
-  long nc = C.ndof;
+  const long nc = C.ndof;
+  const long sites = (long)C.E0 * C.E1;
+  const CoarseGeom cg{C.E0, C.E1, C.nc};
   B.X = mg_alloc(mg, nc * kMaxBatch);
   B.R = mg_alloc(mg, nc * kMaxBatch);
   B.P = mg_alloc(mg, nc * kMaxBatch);
-  B.Rf = (float2*)mg_alloc(mg, (nc * kMaxBatch + 1) / 2);
-  B.Pf = (float2*)mg_alloc(mg, (nc * kMaxBatch + 1) / 2);
-  long ysz = (long)C.E0 * C.E1 * 5 * C.nc * C.nc;
-  B.Yf = (float2*)mg_alloc(mg, (ysz + 1) / 2);
-  launch_to_f32(C.Y, B.Yf, ysz, mg->ctx->stream);
-  B.Yd = (float2*)mg_alloc(mg, (ysz + 1) / 2);
-  launch_adjoint_f32(CoarseGeom{C.E0, C.E1, C.nc}, C.Y, B.Yd, mg->ctx->stream);
+  const char* fp32 = std::getenv("SW_BATCH_FP32");
+  if (tc_supported(C.nc) && !(fp32 && fp32[0] == '1')) {
+    // tensor-core kernel: stacked TF32 blocks of A and A^dag, right-hand-side tiles
+    const long tiles = sites * 5 * tc_tile_floats(C.nc);
+    B.At = (float*)mg_alloc(mg, (tiles + 3) / 4);
+    B.Ad = (float*)mg_alloc(mg, (tiles + 3) / 4);
+    launch_stack_tiles(cg, C.Y, B.At, 0, c->stream);
+    launch_stack_tiles(cg, C.Y, B.Ad, 1, c->stream);
+    const long vt = sites * 2L * kMaxBatch * C.nc;
+    B.Rt = (float*)mg_alloc(mg, (vt + 3) / 4);
+    B.Pt = (float*)mg_alloc(mg, (vt + 3) / 4);
+  } else {
+    // CUDA-core FP32 kernel: FP32 forward and adjoint blocks
+    B.Rf = (float2*)mg_alloc(mg, (nc * 16 + 1) / 2);
+    B.Pf = (float2*)mg_alloc(mg, (nc * 16 + 1) / 2);
+    long ysz = sites * 5 * C.nc * C.nc;
+    B.Yf = (float2*)mg_alloc(mg, (ysz + 1) / 2);
+    launch_to_f32(C.Y, B.Yf, ysz, c->stream);
+    B.Yd = (float2*)mg_alloc(mg, (ysz + 1) / 2);
+    launch_adjoint_f32(cg, C.Y, B.Yd, c->stream);
+  }
   int sms = 0;
-  SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mg->ctx->device));
-  B.partials = (double*)mg_alloc(mg, (long)kMaxBatch * sms);  // 2 phases x 16 x SMs doubles
+  SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  B.partials = (double*)mg_alloc(mg, (long)kMaxBatch * sms);  // 2 phases x 64 x SMs doubles
   B.bar = (unsigned*)mg_alloc(mg, 1);
-  B.status = (int*)mg_alloc(mg, 5);
-  B.dptr = (double2**)mg_alloc(mg, 16);
+  B.status = (int*)mg_alloc(mg, (2 + kMaxBatch + 3) / 4);
+  B.dptr = (double2**)mg_alloc(mg, kMaxBatch);  // 2 x 64 pointers
   B.bps = mg_alloc(mg, N * kMaxBatch);
   B.xps = mg_alloc(mg, N * kMaxBatch);
   B.lex = mg_alloc(mg, N * kMaxBatch);
-  B.nb = kMaxBatch;
+  B.shared = true;
 }
 
 }  // namespace
@@ -899,10 +1068,10 @@ int mg_solve_batch_device(sw_mg* mg, int nb, const double2* Bl, double2* Xl, dou
   sw_ctx* c = mg->ctx;
   sw_gauge* g = mg->g;
   cudaStream_t s = c->stream;
-  SW_REQUIRE(nb >= 1 && nb <= kMaxBatch, SW_ERR_ARG, "batch of 1..16 right-hand sides");
+  SW_REQUIRE(nb >= 1 && nb <= kMaxBatch, SW_ERR_ARG, "batch of 1..64 right-hand sides");
   SW_REQUIRE(mg->mixed && !mg->fine_D, SW_ERR_ARG, "batched solves need a mixed hierarchy");
   auto t0 = std::chrono::steady_clock::now();
-  batch_alloc(mg);
+  batch_alloc(mg, nb);
   BatchWs& B = mg->batch;
   long N = g->N, half = N / 2;
   MgLevel& L = mg->lev[0];
@@ -910,7 +1079,7 @@ int mg_solve_batch_device(sw_mg* mg, int nb, const double2* Bl, double2* Xl, dou
     launch_pack(g, Bl + (long)r * N, B.bps + (long)r * N, s);
     blas_norm2(c, B.bps + (long)r * N, N, slot_base(0) + page(r) + 40);
   }
-  const double2* hs = slots_read_all(c);
+  const double2* hs = slots_read_all(c, nb);
   std::vector<double> bn(nb), tol_abs(nb);
   Set all;
   for (int r = 0; r < nb; ++r) {
@@ -953,7 +1122,7 @@ int mg_solve_batch_device(sw_mg* mg, int nb, const double2* Bl, double2* Xl, dou
     blas_sub(c, t, Bl + (long)r * N, t, N);
     blas_norm2(c, t, N, slot_base(0) + page(r) + 41);
   }
-  const double2* hs2 = slots_read_all(c);
+  const double2* hs2 = slots_read_all(c, nb);
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   bool ok = true;
   for (int r = 0; r < nb; ++r) {
@@ -974,4 +1143,33 @@ int mg_solve_batch_device(sw_mg* mg, int nb, const double2* Bl, double2* Xl, dou
     o.seconds = secs;
   }
   return ok ? SW_OK : SW_ERR_NOCONV;
+}
+
+int mg_batch_stall(sw_mg* mg, int nb) {
+  SW_REQUIRE(nb >= 1 && nb <= kMaxBatch, SW_ERR_ARG, "batch of 1..64 right-hand sides");
+  SW_REQUIRE(mg->mixed && !mg->fine_D, SW_ERR_ARG, "batched solves need a mixed hierarchy");
+  batch_alloc(mg, nb);
+  const int l = mg->nlev - 1;
+  for (int r = 0; r < nb; ++r) blas_zero(mg->ctx, mg->batch.lv[l][r].rhs, level_len(mg, l));
+  Set set;
+  for (int r = 0; r < nb; ++r) set.push_back(r);
+  BatchCounters bc(kMaxBatch);
+  cgne_b(mg, l, set, bc, 1);
+  return SW_OK;
+}
+
+int mg_autotune_entries(int max, int* nc, int* K, int* sites, int* stages, double* us) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  int n = 0;
+  for (const auto& kv : g_tune) {
+    if (n < max) {
+      if (nc) nc[n] = std::get<1>(kv.first);
+      if (K) K[n] = std::get<2>(kv.first);
+      if (sites) sites[n] = std::get<3>(kv.first);
+      if (stages) stages[n] = kv.second.stages;
+      if (us) us[n] = kv.second.us_per_iter;
+    }
+    ++n;
+  }
+  return n;
 }

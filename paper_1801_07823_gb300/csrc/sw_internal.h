@@ -80,8 +80,8 @@ __device__ __forceinline__ double2 coef_eval(const double2* S, Coef c) {
 }
 
 constexpr int kSlotPage = 320;  // 64 per multigrid level (up to 4), 64 for other solvers
-constexpr int kMaxBatch = 16;   // right-hand sides solved together by sw_mg_solve_batch
-constexpr int kNumSlots = kSlotPage * (kMaxBatch + 1);  // page 0: single solves; 1..16: batch
+constexpr int kMaxBatch = 64;   // right-hand sides solved together by sw_mg_solve_batch
+constexpr int kNumSlots = kSlotPage * (kMaxBatch + 1);  // page 0: single solves; 1..64: batch
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so every sum has one order
 
 // Per-category kernel timing with CUDA events on the context stream.
@@ -258,6 +258,18 @@ bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const 
                             double* partials, unsigned* bar, int* status, int maxit, double tol,
                             int device, cudaStream_t s, int stall_test = 0);
 
+// FP64 coarsest CGNE in one persistent kernel (cgne64.cu).  variant 1: three
+// real FMAs per complex product, reading Ys = Re + Im of every entry of Y
+// (launch_sum_planes); variant 0: four FMAs on Y alone (Ys may be NULL).
+// v4: 8 n doubles of 32-byte aligned scratch (forms of r and p).  False when
+// nc has no compiled variant.
+bool cgne64_supported(int nc);
+void launch_sum_planes(const double2* Y, double* Ys, long n, cudaStream_t s);
+bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const double* Ys,
+                   const double2* b, double2* x, double2* r, double2* p, double* v4,
+                   double* partials, unsigned* bar, int* status, int maxit, double tol,
+                   int device, cudaStream_t s, int stall_test = 0);
+
 // Batched coarsest CGNE (batch_cgne.cu): nb <= 16 right-hand sides, FP32
 // forward stencil Yf and adjoint stencil Yd (launch_adjoint_f32), FP64
 // iterates.  X, R, P: [n][K] double2; Rf, Pf: n K float2 of scratch (the
@@ -269,6 +281,22 @@ bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, 
                        const double2* const* b, double2* const* x, double2* X, double2* R,
                        double2* P, float2* Rf, float2* Pf, double* partials, unsigned* bar,
                        int* status, int maxit, double tol, int device, cudaStream_t s);
+// Batched coarsest CGNE on the tensor cores (batch_tc.cu): nb <= 64
+// right-hand sides padded to the width tc_width(nb) in {8, 16, 32, 64}.
+// At / Ad: stacked TF32 tiles (launch_stack_tiles, tc_tile_floats(nc) floats
+// per (site, direction)); Rt / Pt: sites x 2 K x nc floats of scratch; X, R, P:
+// [n][K] double2; partials: 2 K SMs doubles; status: 2 + 64 ints ([0] wait
+// timeout or misaligned buffer, [1] non-finite, [2 + r] iterations).
+// stages: pipeline depth, one of tc_stage_options(nc, K).
+int tc_width(int nb);
+bool tc_supported(int nc);
+long tc_tile_floats(int nc);
+int tc_stage_options(int nc, int K, int* out);
+void launch_stack_tiles(const CoarseGeom& g, const double2* Y, float* T, int adj, cudaStream_t s);
+bool launch_cgne_tc(const CoarseGeom& g, int stages, const float* At, const float* Ad, int nb,
+                    const double2* const* b, double2* const* x, double2* X, double2* R,
+                    double2* P, float* Rt, float* Pt, double* partials, unsigned* bar,
+                    int* status, int maxit, double tol, int device, cudaStream_t s, int stall);
 // Yd[X][d] = Y[nb(X, d)][opp(d)]^dag in FP32, every block column-major like Y.
 void launch_adjoint_f32(const CoarseGeom& g, const double2* Y, float2* Yd, cudaStream_t s);
 

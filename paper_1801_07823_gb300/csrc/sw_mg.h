@@ -18,6 +18,8 @@ struct MgLevel {
   float* Ysc = nullptr;   // ... with one scale per block
   float4* Ydf = nullptr;  // mixed precision, coarsest level: double-float stencil
   float4* cdf = nullptr;  // [2][ndof] double-float copies of r and p for its CGNE
+  double* Ys = nullptr;   // coarsest level: Re + Im of every stencil entry (FP64 CGNE)
+  double* c4 = nullptr;   // coarsest level: [2][ndof][4] vector forms of its FP64 CGNE
   // setup work vectors
   double2 *sr = nullptr, *sp = nullptr, *sq = nullptr, *st = nullptr;
   // solve work vectors
@@ -40,6 +42,7 @@ struct LevelWs {
 // Workspace of batched solves (allocated on the first one).
 struct BatchWs {
   int nb = 0;                            // right-hand sides the workspace holds
+  bool shared = false;                   // the arrays shared by all right-hand sides exist
   std::vector<std::vector<LevelWs>> lv;  // [level][rhs]
   double2 *X = nullptr, *R = nullptr, *P = nullptr;  // coarsest CGNE, [n][K]
   float2 *Rf = nullptr, *Pf = nullptr;
@@ -48,7 +51,9 @@ struct BatchWs {
   double* partials = nullptr;
   unsigned* bar = nullptr;
   int* status = nullptr;
-  double2** dptr = nullptr;              // device arrays of b and x pointers, [2][16]
+  double2** dptr = nullptr;              // device arrays of b and x pointers, [2][64]
+  float *At = nullptr, *Ad = nullptr;    // stacked TF32 tiles of the coarsest A and A^dag
+  float *Rt = nullptr, *Pt = nullptr;    // TF32 right-hand-side tiles of r and p
   double2 *bps = nullptr, *xps = nullptr, *lex = nullptr;  // [16][N] fine buffers
 };
 
@@ -90,8 +95,12 @@ void mg_setup(sw_mg* mg, const double* const* psi0, uint64_t seed);
 int mg_coarsest_solve(sw_mg* mg, const double2* b, double2* x);  // CGNE on the coarsest level
 int mg_solve_device(sw_mg* mg, const double2* b_lex, double2* x_lex, double tol,
                     sw_solve_stats* st);
-// nb (<= 16) right-hand sides of a mixed-precision hierarchy in lockstep, the
+// nb (<= 64) right-hand sides of a mixed-precision hierarchy in lockstep, the
 // coarsest solves of all of them in one batched kernel.  B, X: [nb][N]
 // lexicographic device buffers; st: [nb] or NULL.
 int mg_solve_batch_device(sw_mg* mg, int nb, const double2* B, double2* X, double tol,
                           sw_solve_stats* st);
+// Failure-detection check of the batched coarsest kernel (sw_debug_batch_stall).
+int mg_batch_stall(sw_mg* mg, int nb);
+// Autotuner records: (nc, K, sites, stages, microseconds per iteration).
+int mg_autotune_entries(int max, int* nc, int* K, int* sites, int* stages, double* us);

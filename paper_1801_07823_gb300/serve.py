@@ -65,8 +65,12 @@ def hierarchy_bytes(L: int, blocks, nvec, mixed: bool, outer_restart: int = 32,
 
 def batch_workspace_bytes(L: int, blocks, nvec, outer_restart: int = 32,
                           inter_restart: int = 8, width: int = 16) -> int:
-    """Device bytes of the workspace of batched solves (allocated on the first
-    one, for `width` right-hand sides), from the sizes of its arrays."""
+    """Device bytes of the workspace of batched solves, from the sizes of its
+    arrays: per-right-hand-side work vectors for `width` right-hand sides
+    (grown on demand), plus the arrays every batch shares, which are sized for
+    the widest batch (64): the coarsest iterates, the stacked TF32 stencil tiles
+    of A and A^dag, the TF32 right-hand-side tiles and the fine staging
+    buffers."""
     N = L * L
     lens = [N // 2]                                 # level 1: even half of the fine lattice
     E, nc = L, 1
@@ -80,11 +84,13 @@ def batch_workspace_bytes(L: int, blocks, nvec, outer_restart: int = 32,
         nbas = 0 if last else (outer_restart if l == 0 else inter_restart)
         per_rhs = 2 if last else 2 + 2 + 2 * nbas + 6
         b += width * per_rhs * n * 16
-    nc_last = lens[-1]
-    sites = nc_last // nc
-    b += 3 * nc_last * width * 16 + 2 * nc_last * width * 8    # iterates, FP32 stencil inputs
-    b += 2 * sites * 5 * nc * nc * 8                          # FP32 stencil and adjoint blocks
-    b += 3 * N * width * 16                                   # fine staging buffers
+    wmax = 64
+    n_last = lens[-1]
+    sites = n_last // nc
+    b += 3 * n_last * wmax * 16                     # iterates X, R, P
+    b += 2 * sites * 5 * 128 * nc * 4               # stacked TF32 tiles of A and A^dag
+    b += 2 * sites * 2 * wmax * nc * 4              # TF32 right-hand-side tiles of r and p
+    b += 3 * N * wmax * 16                          # fine staging buffers
     return int(b)
 
 
