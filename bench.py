@@ -107,7 +107,14 @@ def parse():
                     help="run only the Dslash bandwidth microbenchmark")
     ap.add_argument("--batch-reps", type=int, default=3,
                     help="timed batches per batch width")
-    ap.add_argument("--serving-requests", type=int, default=32,
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving measurement (with the options below)")
+    ap.add_argument("--serving-workers", type=int, default=2)
+    ap.add_argument("--serving-batch", type=int, default=8)
+    ap.add_argument("--serving-rate", type=float, default=4.0)
+    ap.add_argument("--serving-fp64", action="store_true",
+                    help="serve with FP64 hierarchies (the plain baseline of the served form)")
+    ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests of the serving measurement (0: skip it)")
     return ap.parse_args()
 
@@ -217,6 +224,60 @@ def oracle_solve_seconds(H, rec, reps):
     return rec["overhead_ratio"] * sum(c[k] * ta[k] for k in c), ta
 
 
+def cpu_model() -> str:
+    """CPU model name of this host (lscpu, else /proc/cpuinfo) and its core count."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{name or 'unknown'}, nproc {os.cpu_count()}"
+
+
+def oracle_validation(sizes=(32, 64)):
+    """Measured full single-core oracle solves at small lattices (3 levels, the
+    paper's Nv 8/12, beta 6, m = 0.01, tol 1e-10), each beside the prediction
+    of the model that extrapolates the 256^2 figure (application counts x
+    per-application times here x the 256^2 solve's wall/application ratio)."""
+    import sw_inputs as si
+    from oracle import mg as omg
+    from oracle.solve_counts import _Counted, apply_times
+    rec = oracle_counts(WORKLOAD["L"])
+    out = []
+    for L in sizes:
+        blocks, nvec = [(4, 4), (2, 2)], [8, 12]
+        th = si.heatbath_u1(L, L, 6.0, 200, seed=1, device="cpu")
+        psi0 = si.null_vector_guesses(L, L, nvec, 3, blocks)
+        H = omg.Hierarchy(th, 0.01, 3, blocks, nvec, [list(a) for a in psi0])
+        for lvl in (1, 2):
+            lev = H.levels[lvl]
+            lev.op, lev.opdag = _Counted(lev.op), _Counted(lev.opdag)
+        b = si.gaussian_complex(1003, L * L)
+        t = time.perf_counter()
+        _, st = H.solve(b, 1e-10)
+        wall = time.perf_counter() - t
+        counts = {"S": st["fine_applies"],
+                  "A2": H.levels[1].op.n + H.levels[1].opdag.n,
+                  "A3": H.levels[2].op.n + H.levels[2].opdag.n}
+        ta = apply_times(H, reps=20)
+        model = rec["overhead_ratio"] * sum(counts[k] * ta[k] for k in counts) if rec else None
+        out.append({"L": L, "measured_s": wall, "model_s": model, "solves_per_s": 1.0 / wall,
+                    "true_resid": float(st["true_resid"]), "converged": bool(st["converged"])})
+    return out
+
+
 def oracle_sample_note(rec, ta, reps):
     c = rec["counts"]
     return (f"{reps} applications each of the oracle's S, A_hat2, A_hat3 timed here "
@@ -262,44 +323,94 @@ def dslash_bandwidth(sw, ctx, L=4096, reps=20):
     return out
 
 
-def serving_measurement(nreq, seed=11):
-    """Poisson request stream over 4 resident gauge fields (64^2 and 128^2;
-    beta 6 and 10, 200 heatbath sweeps) with masses log-uniform in [1e-2, 1e-1]
-    served on the mass grid {1e-2, 3e-2, 1e-1}; 2 worker streams;
-    mixed-precision hierarchies with the paper's Table kcycle parameters
-    (Nv 8/12); tol 1e-10.  Latency = finish - arrival, hierarchy setups on first
-    use included."""
+SERVING_FIELDS = [(64, 3.0), (64, 6.0), (128, 6.0), (128, 10.0), (256, 6.0), (256, 10.0),
+                  (512, 6.0), (512, 10.0)]
+SERVING_MASSES = [1e-3, 1e-2, 1e-1]
+
+
+def coarse_stencil_bandwidth(sw, ctx, L=1024, reps=20):
+    """Coarse-stencil microbenchmark: the level-2 stencil of a 1024^2 hierarchy
+    (4x4 KD-block aggregates, Nv 24: 128^2 coarse sites x 48 dof, stencil larger
+    than L2) applied in FP64 and in scaled FP16 (mixed hierarchy), timed with the
+    library's CUDA-event brackets around each application.  Algorithmic bytes
+    per coarse site and application: 5 nc^2 p for the blocks (p = 16 B FP64, 4 B
+    FP16 plus 5 x 4 B of block scales) + 2 nc x 16 B for the vectors."""
+    import torch
+    gen = torch.Generator(device="cuda").manual_seed(1024)
+    theta = (torch.rand((2, L, L), generator=gen, device="cuda", dtype=torch.float64) * 2 - 1) * math.pi
+    g = sw.sw_gauge_load(ctx, theta)
+    p = sw.sw_mg_params_default()
+    p.setup_maxiter = 2           # the stencil's values do not matter here
+    p.precision = sw.SW_MG_MIXED
+    h = sw.sw_mg_setup(g, 0.01, 3, [(4, 4), (2, 2)], [24, 32], params=p, seed=7)
+    e0, e1, nc = sw.sw_mg_level_info(h, 2)
+    n = e0 * e1 * nc
+    v = torch.randn(n, dtype=torch.complex128, device="cuda", generator=gen)
+    w = torch.empty_like(v)
+    out = {"lattice": f"{L}x{L}", "coarse_sites": e0 * e1, "nc": nc}
+    for name, prec, pb, extra in (("fp64", sw.SW_PREC_FP64, 16, 0), ("fp16s", sw.SW_PREC_FP16S, 4, 20)):
+        for _ in range(3):
+            sw.sw_mg_apply_level(h, 2, prec, 0, v, w)
+        sw.sw_set_timing(ctx, True)
+        for _ in range(reps):
+            sw.sw_mg_apply_level(h, 2, prec, 0, v, w)
+        cnt, ms = sw.sw_kernel_times(ctx, 7)[1]
+        sw.sw_set_timing(ctx, False)
+        t = ms / 1e3 / max(cnt, 1)
+        byt = (5 * nc * nc * pb + extra + 2 * nc * 16) * e0 * e1
+        out[name] = {"GB/s": byt / t / 1e9, "frac_of_hbm": byt / t / 1e9 / HBM_PEAK_GBS,
+                     "us": t * 1e6, "bytes_per_apply": byt, "applications": cnt}
+    h.free()
+    g.free()
+    return out
+
+
+def serving_measurement(nreq, seed=11, rate=4.0, workers=2, batch_max=8, mixed=True,
+                        fields=None):
+    """Poisson request stream of single-right-hand-side solves over 8 resident
+    gauge fields (64^2 to 512^2, beta 3, 6 and 10, 200 heatbath sweeps) with
+    cached hierarchies (3 levels, 4x4 then 2x2 aggregates, Nv 24/32, coarsest
+    cap 2048), masses log-uniform in [1e-3, 1e-1] served on the grid
+    {1e-3, 1e-2, 1e-1}, tol 1e-10.  Every hierarchy belongs to one of the
+    worker streams (affinity), is set up before the stream starts (reported as
+    setup_s) and batches the requests queued on it (batch_max); each worker's
+    coarsest kernels hold 1/workers of the SMs.  Latency = finish - arrival."""
     import sw_inputs as si
     from paper_1801_07823_gb300 import serve
-    sizes, betas = [64, 128, 64, 128], [6.0, 6.0, 10.0, 10.0]
+    fields = fields or SERVING_FIELDS
     gauges = [(si.heatbath_u1(L, L, b, 200, seed=100 + i, device="cuda"), f"{L}^2 beta={b}")
-              for i, (L, b) in enumerate(zip(sizes, betas))]
+              for i, (L, b) in enumerate(fields)]
     rng = np.random.default_rng(seed)
     reqs = []
     for i in range(nreq):
         gid = int(rng.integers(len(gauges)))
-        L = sizes[gid]
-        m = float(np.exp(rng.uniform(np.log(1e-2), np.log(1e-1))))
+        L = fields[gid][0]
+        m = float(np.exp(rng.uniform(np.log(1e-3), np.log(1e-1))))
         reqs.append((gid, m, si.gaussian_complex(2000 + i, L * L)))
-    nv = [8, 12]
-
-    def psi0_fn(L):
-        out = [np.stack([si.gaussian_complex(si.stream_seed(5, 0, i), L * L) for i in range(nv[0])])]
-        E = L // 8
-        out.append(np.stack([si.gaussian_complex(si.stream_seed(5, 1, i), E * E * 2 * nv[0])
-                             for i in range(nv[1])]))
-        return out
-
-    srv = serve.Server(gauges, [1e-2, 3e-2, 1e-1], workers=2, hbm_budget=8 << 30,
-                       nvec=tuple(nv), params=dict(outer_maxiter=200), psi0_fn=psi0_fn)
-    done = serve.poisson_stream(srv, reqs, rate=8.0, seed=seed)
+    nv, blocks = [24, 32], [(4, 4), (2, 2)]
+    psi0_fn = lambda L: si.null_vector_guesses(L, L, nv, 3, blocks)
+    srv = serve.Server(gauges, SERVING_MASSES, workers=workers, hbm_budget=160 << 30,
+                       nvec=tuple(nv), blocks=blocks, mixed=mixed, psi0_fn=psi0_fn,
+                       params=dict(outer_maxiter=400, coarsest_maxiter=2048),
+                       batch_max=batch_max, affinity=True)
+    keys = sorted({(g, srv.snap_mass(m)) for g, m, _ in reqs})
+    setup_s = srv.prewarm(keys)
+    done = serve.poisson_stream(srv, reqs, rate=rate, seed=seed)
     srv.close()
     out = serve.latency_summary(done)
-    out["workload"] = ("Poisson arrivals at 8 requests/s; 4 resident gauge fields (64^2, 128^2; "
-                       "beta 6/10, 200 heatbath sweeps); masses log-uniform [1e-2, 1e-1] served on "
-                       "the grid {1e-2, 3e-2, 1e-1}; 2 worker streams; mixed precision, Nv 8/12; "
-                       "hierarchy setups (on first use) count in the latency")
-    out["setups"] = len({(r.worker, r.gauge, r.mass) for r in done})
+    out["workload"] = (f"{nreq} Poisson arrivals at {rate} requests/s over {len(fields)} resident "
+                       f"gauge fields ({', '.join(f'{L}^2 b{b:g}' for L, b in fields)}; 200 "
+                       "heatbath sweeps); masses log-uniform [1e-3, 1e-1] on the grid "
+                       f"{{1e-3, 1e-2, 1e-1}}; Nv 24/32; {workers} worker streams with "
+                       f"hierarchy affinity; batch_max {batch_max}; "
+                       f"{'mixed precision' if mixed else 'FP64'}; tol 1e-10; hierarchies set "
+                       "up before the stream")
+    out["hierarchies"] = len(keys)
+    out["setup_s"] = setup_s
+    out["by_size"] = {str(L): float(np.percentile([r.finish - r.arrival for r in done
+                                                   if fields[r.gauge][0] == L], 50))
+                      for L in sorted({L for L, _ in fields})
+                      if any(fields[r.gauge][0] == L for r in done)}
     return out
 
 
@@ -339,7 +450,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(WORKLOAD, L=L, sweeps=args.sweeps),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": oracle_sample_note(rec, ta, reps)},
+                             "sample": oracle_sample_note(rec, ta, reps), "cpu": cpu_model(),
+                             "measured_full_solves": oracle_validation()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -380,6 +492,7 @@ def batched_measurement(sw, ctx, hm, nbat, L, rank, world, flush, stream, barrie
     val = job_rate(world, nbat * reps, sec)
     return {
         "value": val, "unit": UNIT, "width": nbat, "batches": reps,
+        "iterates": "f32" if getattr(hm, "batch_iterates", 0) else "f64",
         "ms_per_batch": sec / reps * 1e3,
         "dtype": "f64 outer FGCR, vectors and Krylov scalars; f32 fine smoother; f16 (scaled) "
                  "level-2 stencil; coarsest stencil products tf32 on the tensor cores (f32 "
@@ -394,6 +507,49 @@ def batched_measurement(sw, ctx, hm, nbat, L, rank, world, flush, stream, barrie
                             "us_per_iteration": 1e3 * bk[5][1] / max(bk[6][0], 1),
                             "share": bk[5][1] / max(ms, 1e-9)},
         "speedup_vs_fp64": val / fp64_value}
+
+
+def mass_sweep(sw, g, psi0, B, args, world, stream, barrier, timed, fp64_value, ct, cel):
+    """The workload's masses {0.1, 0.01, 0.001} (the paper's Fig. iterworst
+    comparison): FP64 MG and CG on the even/odd normal system on the same field
+    and right-hand sides, solves/s and fine-operator applications per solve.
+    m = 0.001 reuses the headline measurements; the others time 2 solves each
+    after one warm-up, with a fresh hierarchy per mass."""
+    import torch
+    from paper_1801_07823_gb300 import presets
+    tol = WORKLOAD["tol"]
+    out = {"0.001": {"mg_solves_per_s": fp64_value, "mg_fine_applies": timed[0]["fine_applies"],
+                     "mg_outer_iters": timed[0]["outer_iters"],
+                     "cg_solves_per_s": job_rate(world, args.steps, cel),
+                     "cg_fine_applies": ct[0]["fine_applies"]}}
+    X = torch.zeros_like(B[0])
+    for m in (0.1, 0.01):
+        hm = sw.sw_mg_setup(g, m, 3, WORKLOAD["blocks"], WORKLOAD["nvec"],
+                            params=presets.make_params(sw, presets.FP64_256), psi0=psi0)
+        sw.sw_mg_solve(hm, B[0], X, tol)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        sm_ = [sw.sw_mg_solve(hm, B[k], X, tol) for k in (1, 2)]
+        e1.record(stream)
+        barrier()
+        mg_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        hm.free()
+        sw.sw_cg_eo_solve(g, m, B[0], X, tol)
+        barrier()
+        e0.record(stream)
+        sc = [sw.sw_cg_eo_solve(g, m, B[k], X, tol) for k in (1, 2)]
+        e1.record(stream)
+        barrier()
+        cg_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        out[str(m)] = {"mg_solves_per_s": job_rate(world, 2, mg_s),
+                       "mg_fine_applies": sm_[0]["fine_applies"],
+                       "mg_outer_iters": sm_[0]["outer_iters"],
+                       "mg_converged": all(x["converged"] for x in sm_),
+                       "cg_solves_per_s": job_rate(world, 2, cg_s),
+                       "cg_fine_applies": sc[0]["fine_applies"],
+                       "cg_converged": all(x["converged"] for x in sc)}
+    return out
 
 
 # ---------------------------------------------------------------------------- native
@@ -563,11 +719,25 @@ def run_native(args, rank, world, local):
             variants["batched"][str(nbat)] = batched_measurement(
                 sw, ctx, hm, nbat, L, rank, world, flush, stream, barrier, value, xref,
                 reps=args.batch_reps)
-        best = max(variants["batched"].values(), key=lambda v: v["value"])
-        variants["batched_best"] = {"value": best["value"], "unit": UNIT, "width": best["width"],
-                                    "speedup_vs_fp64": best["value"] / value}
         variants["autotune"] = [dict(zip(("nc", "K", "sites", "stages", "us_per_iter"), e))
                                 for e in sw.sw_autotune_entries()]
+        # the same batches with FP32 iterates in the tensor-core coarsest CGNE
+        p32 = presets.make_params(sw, presets.FP64_256)
+        p32.precision = sw.SW_MG_MIXED
+        p32.batch_iterates = sw.SW_PREC_FP32
+        h32 = sw.sw_mg_setup(g, m, 3, WORKLOAD["blocks"], WORKLOAD["nvec"], params=p32, psi0=psi0)
+        h32.batch_iterates = 1
+        variants["batched_fp32_iterates"] = {}
+        for nbat in (16, 32, 64):
+            variants["batched_fp32_iterates"][str(nbat)] = batched_measurement(
+                sw, ctx, h32, nbat, L, rank, world, flush, stream, barrier, value, xref,
+                reps=args.batch_reps)
+        h32.free()
+        best = max(list(variants["batched"].values()) +
+                   list(variants["batched_fp32_iterates"].values()), key=lambda v: v["value"])
+        variants["batched_best"] = {"value": best["value"], "unit": UNIT, "width": best["width"],
+                                    "iterates": best["iterates"],
+                                    "speedup_vs_fp64": best["value"] / value}
         # the CUDA-core FP32 batched kernel on a second mixed hierarchy, for comparison
         os.environ["SW_BATCH_FP32"] = "1"
         hf = sw.sw_mg_setup(g, m, 3, WORKLOAD["blocks"], WORKLOAD["nvec"], params=pm, psi0=psi0)
@@ -592,12 +762,17 @@ def run_native(args, rank, world, local):
             "converged_all": all(x_["converged"] for x_ in ct),
             "true_resid_max": max(x_["true_resid"] for x_ in ct),
             "mg_fine_applies_vs_cg": f"{timed[0]['fine_applies']} vs {ct[0]['fine_applies']}"}
+        variants["mass_sweep"] = mass_sweep(sw, g, psi0, B, args, world, stream, barrier, timed,
+                                            value, ct, cel)
 
     dslash = None if args.no_variants else dslash_bandwidth(sw, ctx)
+    stencil = None if args.no_variants else coarse_stencil_bandwidth(sw, ctx)
     serving = None
     if args.serving_requests > 0 and rank == 0:
         try:  # a failure here must not cost the headline line
-            serving = serving_measurement(args.serving_requests)
+            serving = serving_measurement(args.serving_requests, rate=args.serving_rate,
+                                          workers=args.serving_workers,
+                                          batch_max=args.serving_batch)
         except Exception as exc:
             serving = {"error": f"{type(exc).__name__}: {exc}"}
 
@@ -614,7 +789,8 @@ def run_native(args, rank, world, local):
                                                                        "BLAS-1 excluded)"}}
             t_cpu, ta = oracle_solve_seconds(oracle_hierarchy(th, m, psi0), rec, reps=5)
             cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": oracle_sample_note(rec, ta, 5)}
+                   "sample": oracle_sample_note(rec, ta, 5), "cpu": cpu_model(),
+                   "measured_full_solves": oracle_validation()}
         s0 = timed[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -639,6 +815,7 @@ def run_native(args, rank, world, local):
             "kernels": kern,
             "variants": variants,
             "dslash": dslash,
+            "coarse_stencil": stencil,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -657,8 +834,18 @@ def main():
         import paper_1801_07823_gb300 as sw
         torch.cuda.set_device(local)
         ctx = sw.sw_context_create(local, torch.cuda.current_stream().cuda_stream)
-        print(json.dumps({"dslash": dslash_bandwidth(sw, ctx)}), flush=True)
+        print(json.dumps({"dslash": dslash_bandwidth(sw, ctx),
+                          "coarse_stencil": coarse_stencil_bandwidth(sw, ctx)}), flush=True)
         ctx.free()
+        return
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(local)
+        out = serving_measurement(args.serving_requests, rate=args.serving_rate,
+                                  workers=args.serving_workers,
+                                  batch_max=1 if args.serving_fp64 else args.serving_batch,
+                                  mixed=not args.serving_fp64)
+        print(json.dumps({"serving": out}), flush=True)
         return
     if args.batched_only:
         import torch

@@ -90,6 +90,12 @@ typedef struct {
                             (P^dag D P, outer FGCR and MR on the full D), the
                             variant Sec. III.B shows to stall; FP64 only.  Level-1
                             transfers then act on all sites. */
+  int batch_iterates;    /* Iterates of the batched coarsest CGNE of sw_mg_solve_batch
+                            on a mixed hierarchy: SW_PREC_FP64 (default) or
+                            SW_PREC_FP32 (x, r, p and their updates in FP32; norms
+                            summed in FP64 from FP32 sums of eight rows; alpha and
+                            beta computed in FP64).  On GB300 the FP64 updates of
+                            wide batches cost more than their stencil products. */
 } sw_mg_params;
 
 /* Per-solve counters.  "fine applies" counts applications of the level-1
@@ -114,6 +120,14 @@ void sw_mg_params_default(sw_mg_params* p);
  * default stream.  Every later call on objects of this context runs on it. */
 int sw_context_create(int device, void* cuda_stream, sw_ctx** out);
 void sw_context_free(sw_ctx* ctx);
+/* Share num/den (0 < num <= den) of the GPU's SMs that the persistent
+ * (cooperative, grid-synchronised) coarsest-level kernels of this context may
+ * hold: they run with one CTA on each of floor(SMs num / den) SMs (at least
+ * one).  Default 1/1.  Persistent kernels of contexts of one process whose
+ * shares fit the SM count together run concurrently; a launch that does not
+ * fit beside the running ones waits for them (host side).  A result depends
+ * on the share (the grid fixes the order of its sums), not on what else runs. */
+int sw_context_set_sm_share(sw_ctx* ctx, int num, int den);
 /* Last error message of the context (never NULL; "" after success). */
 const char* sw_last_error(sw_ctx* ctx);
 
@@ -215,6 +229,14 @@ int sw_debug_maps(sw_gauge* g, int a0, int a1, int32_t* eta, int32_t* eps, int32
  * site (1 on level 1, 2 nvec[l-2] below). */
 int sw_mg_level_info(sw_mg* mg, int level, int* E0, int* E1, int* nc);
 
+/* Integer maps of level l (1 = fine, up to levels - 1) of a hierarchy, as the
+ * transfer kernels compute them, for bit-exact comparison (host buffers of
+ * ndof_l int32 each; ndof_1 = L0 L1 in site order x0 + L0 x1, coarser levels
+ * in dof order X nc + k): agg = the aggregate (site of level l + 1) each dof
+ * belongs to; chir = its chirality, eps(x) on level 1 (Eq. epsilon) and sigma3
+ * (+1 for k < nc/2, -1 above) on coarser levels (Sec. IV, chiral doubling). */
+int sw_mg_level_maps(sw_mg* mg, int level, int32_t* agg, int32_t* chir);
+
 /* Copies of level data, for tests (host buffers, complex128):
  *  P of level l (maps level l+1 to level l), [ndof_l][nvec_l]: row = dof of
  *  level l (fine: site s = x0 + L0 x1; coarser: X * nc + k), entry i = the
@@ -303,7 +325,8 @@ int sw_debug_batch_stall(sw_mg* mg, int nrhs);
 /* Choices of the autotuner in this process: entry k gives the coarse dof per
  * site nc[k], the batch width K[k], the number of coarse sites, the choice and
  * its measured microseconds per CGNE iteration.  For the batched tensor-core
- * coarsest kernel (K = 8, 16, 32 or 64) the choice is its pipeline depth; for
+ * coarsest kernel (K = 8, 16, 32 or 64; 100 + K with FP32 iterates) the
+ * choice is its pipeline depth; for
  * the single-right-hand-side FP64 coarsest kernel (K = 1) it is the product
  * form (0: four real FMAs per complex multiply-add, 1: three, with a stored
  * sum plane).  Fills at most max entries (any pointer may be NULL) and returns

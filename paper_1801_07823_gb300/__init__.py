@@ -23,7 +23,7 @@ __all__ = [
     "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_level", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
     "sw_dslash_schur_noalloc", "sw_debug_cgne_stall", "sw_cg_eo_solve", "sw_debug_batch_stall",
-    "sw_autotune_entries",
+    "sw_autotune_entries", "sw_mg_level_maps", "sw_context_set_sm_share",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S, SW_OP_DNAIK, SW_OP_ANAIK = 0, 1, 2, 3, 4, 5, 6
@@ -48,7 +48,8 @@ class sw_mg_params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("inter_restart", ctypes.c_int),
                 ("inter_maxiter", ctypes.c_int), ("inter_tol", ctypes.c_double),
                 ("coarsest_maxiter", ctypes.c_int), ("coarsest_tol", ctypes.c_double),
-                ("precision", ctypes.c_int), ("fine_operator", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("fine_operator", ctypes.c_int),
+                ("batch_iterates", ctypes.c_int)]
 
 
 class sw_solve_stats(ctypes.Structure):
@@ -103,6 +104,8 @@ def lib():
             "sw_cg_eo_solve": (_I, [_VP, _D, _VP, _VP, _D, _I, _I, ctypes.POINTER(sw_solve_stats)]),
             "sw_debug_batch_stall": (_I, [_VP, _I]),
             "sw_autotune_entries": (_I, [_I, _VP, _VP, _VP, _VP, _VP]),
+            "sw_mg_level_maps": (_I, [_VP, _I, _VP, _VP]),
+            "sw_context_set_sm_share": (_I, [_VP, _I, _I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -420,3 +423,18 @@ def sw_autotune_entries() -> list:
     lib().sw_autotune_entries(n, nc.ctypes.data, K.ctypes.data, sites.ctypes.data,
                               st.ctypes.data, us.ctypes.data)
     return [(int(a), int(b), int(c), int(d), float(e)) for a, b, c, d, e in zip(nc, K, sites, st, us)]
+
+
+def sw_mg_level_maps(mg: _Handle, level: int):
+    """(agg, chir) int32 maps of a level's dofs as the transfer kernels use them."""
+    n = mg.shape[0] * mg.shape[1] if level == 1 else _level_len(mg, level)
+    agg = np.zeros(n, dtype=np.int32)
+    chir = np.zeros(n, dtype=np.int32)
+    _check(lib().sw_mg_level_maps(mg.ptr, int(level), agg.ctypes.data, chir.ctypes.data),
+           mg.ctx_ptr)
+    return agg, chir
+
+
+def sw_context_set_sm_share(ctx: _Handle, num: int, den: int):
+    """Persistent coarsest kernels of this context hold num/den of the SMs."""
+    _check(lib().sw_context_set_sm_share(ctx.ptr, int(num), int(den)), ctx.ptr)

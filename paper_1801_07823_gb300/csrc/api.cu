@@ -129,6 +129,7 @@ void sw_mg_params_default(sw_mg_params* p) {
   p->coarsest_tol = 0.2;
   p->precision = SW_MG_FP64;
   p->fine_operator = SW_MG_COARSEN_A;
+  p->batch_iterates = SW_PREC_FP64;
 }
 
 uint64_t sw_stream_seed(uint64_t seed, int level, int index) {
@@ -371,6 +372,8 @@ int sw_mg_setup(sw_gauge* g, double mass, int levels, const int* block, const in
     mg->mixed = p.precision == SW_MG_MIXED;
     SW_REQUIRE(p.fine_operator == SW_MG_COARSEN_A || p.fine_operator == SW_MG_COARSEN_D,
                SW_ERR_ARG, "unknown fine_operator");
+    SW_REQUIRE(p.batch_iterates == SW_PREC_FP64 || p.batch_iterates == SW_PREC_FP32, SW_ERR_ARG,
+               "batch_iterates must be SW_PREC_FP64 or SW_PREC_FP32");
     mg->fine_D = p.fine_operator == SW_MG_COARSEN_D;
     SW_REQUIRE(!(mg->fine_D && mg->mixed), SW_ERR_ARG,
                "the Galerkin MG of D is provided in FP64 only");
@@ -532,6 +535,25 @@ int sw_mg_level_info(sw_mg* mg, int level, int* E0, int* E1, int* nc) {
   return SW_OK;
 }
 
+int sw_mg_level_maps(sw_mg* mg, int level, int32_t* agg, int32_t* chir) {
+  if (!mg || !agg || !chir || level < 1 || level >= mg->nlev) return SW_ERR_ARG;
+  return guarded(mg->ctx, [&] {
+    const MgLevel& L = mg->lev[level - 1];
+    const long n = level == 1 ? (long)mg->g->N : L.ndof;
+    cudaStream_t s = mg->ctx->stream;
+    ScopedBuffers scratch;
+    int* d = (int*)scratch.get((2 * n + 3) / 4);
+    if (level == 1)
+      launch_level_maps_fine(mg->g, L.b0, L.b1, d, d + n, s);
+    else
+      launch_level_maps_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, d, d + n, s);
+    SW_CUDA(cudaMemcpyAsync(agg, d, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SW_CUDA(cudaMemcpyAsync(chir, d + n, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SW_CUDA(cudaStreamSynchronize(s));
+    return SW_OK;
+  });
+}
+
 int sw_mg_export_P(sw_mg* mg, int level, double* P) {
   if (!mg || !P || level < 1 || level >= mg->nlev) return SW_ERR_ARG;
   return guarded(mg->ctx, [&] {
@@ -599,6 +621,8 @@ int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const voi
       launch_unpack(g, a, b, s);
     } else {
       CoarseGeom cg{L.E0, L.E1, L.nc};
+      // timed like the solver's applications (category level - 1), kernel only
+      const int tk = timing_begin(mg->ctx, level - 1);
       if (precision == SW_PREC_FP64) {
         launch_coarse_apply(cg, L.Y, dagger ? 1 : 0, a, b, s);
       } else if (precision == SW_PREC_FP16S) {
@@ -610,6 +634,7 @@ int sw_mg_apply_level(sw_mg* mg, int level, int precision, int dagger, const voi
       } else {
         throw SwError{SW_ERR_ARG, "unknown precision"};
       }
+      timing_end(mg->ctx, tk);
     }
     SW_CUDA(cudaMemcpyAsync(out, b, n * sizeof(double2),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -674,6 +699,13 @@ int sw_debug_cgne_stall(sw_mg* mg) {
     mg->stall_test = 0;
     return rc;
   });
+}
+
+int sw_context_set_sm_share(sw_ctx* ctx, int num, int den) {
+  if (!ctx || num < 1 || den < 1 || num > den) return SW_ERR_ARG;
+  ctx->sm_num = num;
+  ctx->sm_den = den;
+  return SW_OK;
 }
 
 int sw_debug_batch_stall(sw_mg* mg, int nrhs) {

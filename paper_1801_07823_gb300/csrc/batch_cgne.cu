@@ -569,24 +569,26 @@ __global__ void k_adjoint_f32(const double2* __restrict__ Y, float2* __restrict_
 }
 
 template <int NC, int K>
-bool launch_b(const BatchArgs& args, int device, cudaStream_t s) {
+bool launch_b(const BatchArgs& args, int device, cudaStream_t s, int sms_use) {
   using T = Tile<NC, K>;
-  static int cached_grid[64] = {0};
-  int& grid = cached_grid[device & 63];
-  if (grid == 0) {
-    int occ = 0, sms = 0, coop = 0;
+  static int cached_sms[64] = {0};
+  int& sms = cached_sms[device & 63];
+  if (sms == 0) {
+    int occ = 0, coop = 0, n = 0;
     SW_CUDA(cudaFuncSetAttribute((const void*)k_cgne_batch<NC, K>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, T::kSmem));
     SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne_batch<NC, K>, kThreads,
                                                           T::kSmem));
-    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    SW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device));
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     if (!coop || occ < 1)
       throw SwError{SW_ERR_CUDA, "batched CGNE cannot be launched cooperatively (occupancy " +
                                      std::to_string(occ) + ", cooperative " +
                                      std::to_string(coop) + ")"};
-    grid = sms;  // one CTA per SM for every batch width (see the header note)
+    sms = n;
   }
+  // one CTA per SM it may use, for every batch width (see the header note)
+  const int grid = sms_use < sms ? (sms_use > 0 ? sms_use : 1) : sms;
   BatchArgs a = args;
   void* params[] = {&a};
   SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne_batch<NC, K>, dim3(grid),
@@ -607,7 +609,8 @@ void launch_adjoint_f32(const CoarseGeom& g, const double2* Y, float2* Yd, cudaS
 bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, int nb,
                        const double2* const* b, double2* const* x, double2* X, double2* R,
                        double2* P, float2* Rf, float2* Pf, double* partials, unsigned* bar,
-                       int* status, int maxit, double tol, int device, cudaStream_t s) {
+                       int* status, int maxit, double tol, int device, cudaStream_t s,
+                       int sms_use) {
   if (nb < 1 || nb > 16) return false;
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 18 * sizeof(int), s));
@@ -616,9 +619,9 @@ bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, 
   int K = cgne_batch_width(nb);
 #define SW_CASE(NCV)                                   \
   case NCV:                                            \
-    if (K == 4) return launch_b<NCV, 4>(a, device, s); \
-    if (K == 8) return launch_b<NCV, 8>(a, device, s); \
-    return launch_b<NCV, 16>(a, device, s);
+    if (K == 4) return launch_b<NCV, 4>(a, device, s, sms_use); \
+    if (K == 8) return launch_b<NCV, 8>(a, device, s, sms_use); \
+    return launch_b<NCV, 16>(a, device, s, sms_use);
   switch (g.nc) {
     SW_CASE(16)
     SW_CASE(24)

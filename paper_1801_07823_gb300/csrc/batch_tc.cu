@@ -31,8 +31,9 @@ __global__ void k_stack_tiles(const double2* __restrict__ Y, float* __restrict__
 
 }  // namespace
 
-bool swtc::run_nc64(const TcArgs& a, int K, int S, int device, cudaStream_t s) {
-  return run_nc<64>(a, K, S, device, s);
+bool swtc::run_nc64(const TcArgs& a, int K, int S, bool f32, int device, cudaStream_t s,
+                     int sms_use) {
+  return run_nc<64>(a, K, S, f32, device, s, sms_use);
 }
 
 int tc_width(int nb) { return nb <= 8 ? 8 : (nb <= 16 ? 16 : (nb <= 32 ? 32 : 64)); }
@@ -59,10 +60,11 @@ int tc_stage_options(int nc, int K, int* out) {
   return n;
 }
 
-bool launch_cgne_tc(const CoarseGeom& g, int stages, const float* At, const float* Ad, int nb,
-                    const double2* const* b, double2* const* x, double2* X, double2* R,
+bool launch_cgne_tc(const CoarseGeom& g, int stages, bool f32, const float* At, const float* Ad,
+                    int nb, const double2* const* b, double2* const* x, double2* X, double2* R,
                     double2* P, float* Rt, float* Pt, double* partials, unsigned* bar,
-                    int* status, int maxit, double tol, int device, cudaStream_t s, int stall) {
+                    int* status, int maxit, double tol, int device, cudaStream_t s, int stall,
+                    int sms_use) {
   const int K = tc_width(nb);
   if (nb < 1 || nb > kMaxK || !tc_supported(g.nc)) return false;
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
@@ -70,9 +72,9 @@ bool launch_cgne_tc(const CoarseGeom& g, int stages, const float* At, const floa
   TcArgs a{At, Ad, b, x, X, R, P, Rt, Pt, partials, bar, status, nb, g.E0, g.E1, maxit, tol,
            stall};
   switch (g.nc) {
-    case 16: return run_nc16(a, K, stages, device, s);
-    case 24: return run_nc24(a, K, stages, device, s);
-    case 64: return run_nc64(a, K, stages, device, s);
+    case 16: return run_nc16(a, K, stages, f32, device, s, sms_use);
+    case 24: return run_nc24(a, K, stages, f32, device, s, sms_use);
+    case 64: return run_nc64(a, K, stages, f32, device, s, sms_use);
     default: return false;
   }
 }

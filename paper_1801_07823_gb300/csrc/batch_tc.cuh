@@ -200,9 +200,9 @@ struct TcArgs {
   const float* Ad;         // [sites][5] stacked adjoint blocks
   const double2* const* b; // [K] right-hand sides
   double2* const* xout;    // [K] solutions
-  double2* X;              // [n][K] FP64 iterates
-  double2* R;
-  double2* P;
+  void* X;                 // [n][K] iterates: double2, or float2 with FP32 iterates
+  void* R;
+  void* P;
   float* Rt;               // [sites] 2K x nc TF32 tiles of r (stencil input of A^dag)
   float* Pt;               // [sites] tiles of p (stencil input of A)
   double* partials;        // [2][K][gridDim.x]
@@ -243,6 +243,7 @@ struct TcSmem {
   double cta_sum[K];
   double red[K][8];
   double sum[K], rr[K], stop[K], coef[K];
+  float coef_f[K];                           // coef in FP32 (FP32 iterates)
   int state[K];                              // 0 active, 1 stopped, 2 non-finite
   int iters[K];
   int any;
@@ -304,7 +305,7 @@ struct Pipe {
 
 // One stencil application over this CTA's sites fused with the update of the
 // phase; leaves this CTA's per-right-hand-side norm sums in sm.cta_sum.
-template <int NC, int K, int S, int MODE>
+template <int NC, int K, int S, bool F32, int MODE>
 __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
                          TcSmem<NC, K, S>& sm, Pipe& pp) {
   using C = TcCfg<NC, K, S>;
@@ -419,47 +420,111 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
         const int kg = K < 16 ? K : 16;
         const int ioff = K < 16 ? K : 16;  // column of the first imaginary-part product
         for (int pidx = e; pidx < kg * C::kGroups; pidx += kEpiThreads) {
-          const int r = c0 + pidx % kg, grp = pidx / kg;
-          const int cr = pidx % kg;
-          double q2 = 0.0;
-          for (int i = grp * 8; i < grp * 8 + 8; ++i) {
+          const int cr = pidx % kg, grp = pidx / kg, r = c0 + cr;
+          float* vt = (MODE == kXR ? a.Rt : a.Pt) + (size_t)X * (C::kBTile / 4);
+          const size_t el0 = ((size_t)X * NC + grp * 8) * K + r;  // row grp * 8, step K
+          // the eight rows' products, then all their loads, then the updates
+          float re[8], im[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int i = grp * 8 + k;
             auto E = [&](int row, int col) { return exch[row * 32 + ((col + row) & 31)]; };
-            const float re = E(i, cr) - E(i + NC, ioff + cr);
-            const float im = E(i, ioff + cr) + E(i + NC, cr);
-            const size_t el = ((size_t)X * NC + i) * K + r;
-            float* vt = (MODE == kXR ? a.Rt : a.Pt) + (size_t)X * (C::kBTile / 4);
-            if (MODE == kInit) {
-              const double2 pv = make_double2((double)re, (double)im);
-              a.P[el] = pv;
-              vt[tile_off(r, i, C::kN) / 4] = to_tf32(re);
-              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32(im);
-              q2 += fma(pv.x, pv.x, pv.y * pv.y);
-            } else if (MODE == kXR) {
-              double2 xv = __ldcg(a.X + el), rv = __ldcg(a.R + el);
-              if (sm.state[r] == 0) {
-                const double al = sm.coef[r];
-                const double2 pv = __ldcg(a.P + el);
-                xv.x = fma(al, pv.x, xv.x);
-                xv.y = fma(al, pv.y, xv.y);
-                rv.x = fma(-al, (double)re, rv.x);
-                rv.y = fma(-al, (double)im, rv.y);
-                a.X[el] = xv;
-                a.R[el] = rv;
-                q2 += fma(rv.x, rv.x, rv.y * rv.y);
+            re[k] = E(i, cr) - E(i + NC, ioff + cr);
+            im[k] = E(i, ioff + cr) + E(i + NC, cr);
+          }
+          const bool live = MODE == kInit || sm.state[r] == 0;
+          double q2 = 0.0;
+          if (F32) {
+            float2* Xf = reinterpret_cast<float2*>(a.X);
+            float2* Rf = reinterpret_cast<float2*>(a.R);
+            float2* Pf = reinterpret_cast<float2*>(a.P);
+            float2 xv[8], rv[8], pv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              if (MODE == kXR) {
+                xv[k] = __ldcg(Xf + el0 + k * K);
+                rv[k] = __ldcg(Rf + el0 + k * K);
+                pv[k] = __ldcg(Pf + el0 + k * K);
+              } else if (MODE == kP) {
+                pv[k] = __ldcg(Pf + el0 + k * K);
               }
-              vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)rv.x);
-              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)rv.y);
-            } else {
-              double2 pv = __ldcg(a.P + el);
-              if (sm.state[r] == 0) {
-                const double be = sm.coef[r];
-                pv.x = fma(be, pv.x, (double)re);
-                pv.y = fma(be, pv.y, (double)im);
-                a.P[el] = pv;
-                q2 += fma(pv.x, pv.x, pv.y * pv.y);
+            }
+            const float cf = sm.coef_f[r];
+            float s8 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int i = grp * 8 + k;
+              float2 o;
+              if (MODE == kXR) {
+                o = rv[k];
+                if (live) {
+                  xv[k].x = fmaf(cf, pv[k].x, xv[k].x);
+                  xv[k].y = fmaf(cf, pv[k].y, xv[k].y);
+                  o.x = fmaf(-cf, re[k], o.x);
+                  o.y = fmaf(-cf, im[k], o.y);
+                  Xf[el0 + k * K] = xv[k];
+                  Rf[el0 + k * K] = o;
+                }
+              } else {
+                o = make_float2(re[k], im[k]);
+                if (MODE == kP) {
+                  o = pv[k];
+                  if (live) {
+                    o.x = fmaf(cf, o.x, re[k]);
+                    o.y = fmaf(cf, o.y, im[k]);
+                  }
+                }
+                if (live) Pf[el0 + k * K] = o;
               }
-              vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)pv.x);
-              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)pv.y);
+              if (live) s8 = fmaf(o.x, o.x, fmaf(o.y, o.y, s8));
+              vt[tile_off(r, i, C::kN) / 4] = to_tf32(o.x);
+              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32(o.y);
+            }
+            q2 = (double)s8;
+          } else {
+            double2* Xd = reinterpret_cast<double2*>(a.X);
+            double2* Rd = reinterpret_cast<double2*>(a.R);
+            double2* Pd = reinterpret_cast<double2*>(a.P);
+            double2 xv[8], rv[8], pv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              if (MODE == kXR) {
+                xv[k] = __ldcg(Xd + el0 + k * K);
+                rv[k] = __ldcg(Rd + el0 + k * K);
+                pv[k] = __ldcg(Pd + el0 + k * K);
+              } else if (MODE == kP) {
+                pv[k] = __ldcg(Pd + el0 + k * K);
+              }
+            }
+            const double cd = sm.coef[r];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int i = grp * 8 + k;
+              double2 o;
+              if (MODE == kXR) {
+                o = rv[k];
+                if (live) {
+                  xv[k].x = fma(cd, pv[k].x, xv[k].x);
+                  xv[k].y = fma(cd, pv[k].y, xv[k].y);
+                  o.x = fma(-cd, (double)re[k], o.x);
+                  o.y = fma(-cd, (double)im[k], o.y);
+                  Xd[el0 + k * K] = xv[k];
+                  Rd[el0 + k * K] = o;
+                }
+              } else {
+                o = make_double2((double)re[k], (double)im[k]);
+                if (MODE == kP) {
+                  o = pv[k];
+                  if (live) {
+                    o.x = fma(cd, o.x, (double)re[k]);
+                    o.y = fma(cd, o.y, (double)im[k]);
+                  }
+                }
+                if (live) Pd[el0 + k * K] = o;
+              }
+              if (live) q2 += fma(o.x, o.x, o.y * o.y);
+              vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)o.x);
+              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)o.y);
             }
           }
           sm.sq[r * C::kGroups + grp] = q2;
@@ -498,7 +563,7 @@ __device__ void tc_drain(TcSmem<NC, K, S>& sm) {
   __syncthreads();
 }
 
-template <int NC, int K, int S>
+template <int NC, int K, int S, bool F32>
 __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
   using C = TcCfg<NC, K, S>;
   extern __shared__ __align__(1024) unsigned char dyn[];
@@ -547,8 +612,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
     float* vt = a.Rt + (size_t)X * (C::kBTile / 4);
     for (int r = 0; r < K; ++r) {
       const double2 v = r < a.nb ? a.b[r][dof] : make_double2(0.0, 0.0);
-      a.X[dof * K + r] = make_double2(0.0, 0.0);
-      a.R[dof * K + r] = v;
+      if (F32) {
+        reinterpret_cast<float2*>(a.X)[dof * K + r] = make_float2(0.f, 0.f);
+        reinterpret_cast<float2*>(a.R)[dof * K + r] = make_float2((float)v.x, (float)v.y);
+      } else {
+        reinterpret_cast<double2*>(a.X)[dof * K + r] = make_double2(0.0, 0.0);
+        reinterpret_cast<double2*>(a.R)[dof * K + r] = v;
+      }
       vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)v.x);
       vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)v.y);
     }
@@ -588,13 +658,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
     __syncthreads();
     ph ^= 1;
     // p = A^dag r, ||p||^2
-    tc_phase<NC, K, S, kInit>(a, stages, exch, sm, pp);
+    tc_phase<NC, K, S, F32, kInit>(a, stages, exch, sm, pp);
     if (t < K) a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = sm.cta_sum[t];
     go = !aborted(sm) && grid_barrier_tc(a.bar, a.status, ++gen);
   }
   if (go) {
     grid_sums_tc<K>(a.partials + ph * K * gridDim.x, sm.sum);
-    if (t < K) sm.coef[t] = sm.rr[t] / sm.sum[t];  // alpha
+    if (t < K) {
+      sm.coef[t] = sm.rr[t] / sm.sum[t];  // alpha
+      sm.coef_f[t] = (float)sm.coef[t];
+    }
     if (t == 0) {
       int any = 0;
       for (int r = 0; r < K; ++r) any |= sm.state[r] == 0;
@@ -603,7 +676,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
     __syncthreads();
     ph ^= 1;
     while (sm.any) {
-      tc_phase<NC, K, S, kXR>(a, stages, exch, sm, pp);  // w = A p; x += alpha p; r -= alpha w
+      tc_phase<NC, K, S, F32, kXR>(a, stages, exch, sm, pp);  // w = A p; x += alpha p; r -= alpha w
       if (t < K) a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = sm.cta_sum[t];
       if (aborted(sm) || !grid_barrier_tc(a.bar, a.status, ++gen)) {
         go = false;
@@ -618,6 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
         else if (!(k < a.maxit && sqrt(rr_new) > sm.stop[t]))
           sm.state[t] = 1;
         sm.coef[t] = rr_new / sm.rr[t];  // beta
+        sm.coef_f[t] = (float)sm.coef[t];
         sm.rr[t] = rr_new;
       }
       __syncthreads();
@@ -629,14 +703,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
       __syncthreads();
       ph ^= 1;
       if (!sm.any) break;
-      tc_phase<NC, K, S, kP>(a, stages, exch, sm, pp);  // p = A^dag r + beta p
+      tc_phase<NC, K, S, F32, kP>(a, stages, exch, sm, pp);  // p = A^dag r + beta p
       if (t < K) a.partials[(ph * K + t) * gridDim.x + blockIdx.x] = sm.cta_sum[t];
       if (aborted(sm) || !grid_barrier_tc(a.bar, a.status, ++gen)) {
         go = false;
         break;
       }
       grid_sums_tc<K>(a.partials + ph * K * gridDim.x, sm.sum);
-      if (t < K && sm.state[t] == 0) sm.coef[t] = sm.rr[t] / sm.sum[t];  // alpha
+      if (t < K && sm.state[t] == 0) {
+        sm.coef[t] = sm.rr[t] / sm.sum[t];  // alpha
+        sm.coef_f[t] = (float)sm.coef[t];
+      }
       __syncthreads();
       ph ^= 1;
     }
@@ -656,30 +733,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne_tc(TcArgs a) {
                  : "memory");
   if (!go) return;
   for (long dof = tid; dof < n; dof += nthr)
-    for (int r = 0; r < a.nb; ++r) a.xout[r][dof] = __ldcg(a.X + dof * K + r);
+    for (int r = 0; r < a.nb; ++r) {
+      if (F32) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(a.X) + dof * K + r);
+        a.xout[r][dof] = make_double2((double)v.x, (double)v.y);
+      } else {
+        a.xout[r][dof] = __ldcg(reinterpret_cast<const double2*>(a.X) + dof * K + r);
+      }
+    }
   if (blockIdx.x == 0 && t < K) {
     if (sm.state[t] == 2) atomicExch(a.status + 1, 1);
     a.status[2 + t] = sm.iters[t];
   }
 }
 
-template <int NC, int K, int S>
+template <int NC, int K, int S, bool F32>
 void launch_tc_t(const TcArgs& args, int grid, cudaStream_t s) {
   using C = TcCfg<NC, K, S>;
   TcArgs a = args;
   void* params[] = {&a};
-  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne_tc<NC, K, S>, dim3(grid),
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne_tc<NC, K, S, F32>, dim3(grid),
                                       dim3(kThreads), params, C::kSmem, s));
   sw_count_launch();
 }
 
-template <int NC, int K, int S>
+template <int NC, int K, int S, bool F32>
 bool prepare_t(int device, int& grid) {
   using C = TcCfg<NC, K, S>;
   int occ = 0, sms = 0, coop = 0;
-  SW_CUDA(cudaFuncSetAttribute((const void*)k_cgne_tc<NC, K, S>,
+  SW_CUDA(cudaFuncSetAttribute((const void*)k_cgne_tc<NC, K, S, F32>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
-  SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne_tc<NC, K, S>, kThreads,
+  SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne_tc<NC, K, S, F32>, kThreads,
                                                         C::kSmem));
   SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
@@ -690,32 +774,40 @@ bool prepare_t(int device, int& grid) {
 
 // Launches the kernel of one (NC, K, S) on the first call per device after
 // checking that it fits; false if it cannot run cooperatively.
-template <int NC, int K, int S>
-bool run_t(const TcArgs& a, int device, cudaStream_t s) {
+template <int NC, int K, int S, bool F32>
+bool run_t(const TcArgs& a, int device, cudaStream_t s, int sms_use) {
   static int grids[64] = {0};
-  int& grid = grids[device & 63];
-  if (!grid && !prepare_t<NC, K, S>(device, grid)) return false;
-  launch_tc_t<NC, K, S>(a, grid, s);
+  int& sms = grids[device & 63];
+  if (!sms && !prepare_t<NC, K, S, F32>(device, sms)) return false;
+  launch_tc_t<NC, K, S, F32>(a, sms_use < sms ? (sms_use > 0 ? sms_use : 1) : sms, s);
   return true;
 }
 
 // Dispatch over the widths and depths compiled for one NC (one translation
 // unit per NC, so that they compile in parallel).
-template <int NC>
-bool run_nc(const TcArgs& a, int K, int S, int device, cudaStream_t s) {
-  if (K == 8 && S == 2) return run_t<NC, 8, 2>(a, device, s);
-  if (K == 8 && S == 4) return run_t<NC, 8, 4>(a, device, s);
-  if (K == 16 && S == 2) return run_t<NC, 16, 2>(a, device, s);
-  if (K == 16 && S == 4) return run_t<NC, 16, 4>(a, device, s);
-  if (K == 32 && S == 2) return run_t<NC, 32, 2>(a, device, s);
-  if (K == 32 && S == 3) return run_t<NC, 32, 3>(a, device, s);
-  if (K == 64 && S == 2) return run_t<NC, 64, 2>(a, device, s);
-  if (K == 64 && S == 3) return run_t<NC, 64, 3>(a, device, s);
+template <int NC, bool F32>
+bool run_ncf(const TcArgs& a, int K, int S, int device, cudaStream_t s, int sms_use) {
+  if (K == 8 && S == 2) return run_t<NC, 8, 2, F32>(a, device, s, sms_use);
+  if (K == 8 && S == 4) return run_t<NC, 8, 4, F32>(a, device, s, sms_use);
+  if (K == 16 && S == 2) return run_t<NC, 16, 2, F32>(a, device, s, sms_use);
+  if (K == 16 && S == 4) return run_t<NC, 16, 4, F32>(a, device, s, sms_use);
+  if (K == 32 && S == 2) return run_t<NC, 32, 2, F32>(a, device, s, sms_use);
+  if (K == 32 && S == 3) return run_t<NC, 32, 3, F32>(a, device, s, sms_use);
+  if (K == 64 && S == 2) return run_t<NC, 64, 2, F32>(a, device, s, sms_use);
+  if (K == 64 && S == 3) return run_t<NC, 64, 3, F32>(a, device, s, sms_use);
   return false;
 }
+template <int NC>
+bool run_nc(const TcArgs& a, int K, int S, bool f32, int device, cudaStream_t s, int sms_use) {
+  return f32 ? run_ncf<NC, true>(a, K, S, device, s, sms_use)
+             : run_ncf<NC, false>(a, K, S, device, s, sms_use);
+}
 
-bool run_nc16(const TcArgs& a, int K, int S, int device, cudaStream_t s);
-bool run_nc24(const TcArgs& a, int K, int S, int device, cudaStream_t s);
-bool run_nc64(const TcArgs& a, int K, int S, int device, cudaStream_t s);
+bool run_nc16(const TcArgs& a, int K, int S, bool f32, int device, cudaStream_t s,
+              int sms_use);
+bool run_nc24(const TcArgs& a, int K, int S, bool f32, int device, cudaStream_t s,
+              int sms_use);
+bool run_nc64(const TcArgs& a, int K, int S, bool f32, int device, cudaStream_t s,
+              int sms_use);
 
 }  // namespace swtc

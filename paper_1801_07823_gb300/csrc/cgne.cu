@@ -391,18 +391,19 @@ __global__ void k_coarse_apply_df(const float4* __restrict__ Y, const double2* _
 }
 
 template <int NC, bool DF>
-bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s) {
-  static int cached_grid[64] = {0};
-  int& grid = cached_grid[device & 63];
-  if (grid == 0) {
-    int occ = 0, sms = 0;
+bool launch_cgne_t(const CgneArgs& args, int device, cudaStream_t s, int sms_use) {
+  static int cached_per_sm[64] = {0}, cached_sms[64] = {0};
+  int& per_sm = cached_per_sm[device & 63];
+  int& sms = cached_sms[device & 63];
+  if (per_sm == 0) {
+    int occ = 0, coop = 0;
     SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne<NC, DF>, kWarps * 32, 0));
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-    int coop = 0;
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     if (!coop || occ < 1) return false;
-    grid = sms * (occ < 2 ? occ : 2);
+    per_sm = occ < 2 ? occ : 2;
   }
+  const int grid = (sms_use < sms ? (sms_use > 0 ? sms_use : 1) : sms) * per_sm;
   CgneArgs a = args;
   void* params[] = {&a};
   SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne<NC, DF>, dim3(grid), dim3(kWarps * 32),
@@ -431,27 +432,27 @@ void launch_coarse_apply_df(const CoarseGeom& g, const float4* Y, int dagger, co
 bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const double2* b,
                             double2* x, double2* r, double2* p, float4* rdf, float4* pdf,
                             double* partials, unsigned* bar, int* status, int maxit, double tol,
-                            int device, cudaStream_t s, int stall_test) {
+                            int device, cudaStream_t s, int stall_test, int sms_use) {
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));
   CgneArgs a{Y, b, x, r, p, rdf, pdf, partials, bar, status, g.E0, g.E1, maxit, tol, stall_test};
   if (df64) {
     if (!rdf || !pdf) return false;
     switch (g.nc) {
-      case 16: return launch_cgne_t<16, true>(a, device, s);
-      case 24: return launch_cgne_t<24, true>(a, device, s);
-      case 32: return launch_cgne_t<32, true>(a, device, s);
-      case 48: return launch_cgne_t<48, true>(a, device, s);
-      case 64: return launch_cgne_t<64, true>(a, device, s);
+      case 16: return launch_cgne_t<16, true>(a, device, s, sms_use);
+      case 24: return launch_cgne_t<24, true>(a, device, s, sms_use);
+      case 32: return launch_cgne_t<32, true>(a, device, s, sms_use);
+      case 48: return launch_cgne_t<48, true>(a, device, s, sms_use);
+      case 64: return launch_cgne_t<64, true>(a, device, s, sms_use);
       default: return false;
     }
   }
   switch (g.nc) {
-    case 16: return launch_cgne_t<16, false>(a, device, s);
-    case 24: return launch_cgne_t<24, false>(a, device, s);
-    case 32: return launch_cgne_t<32, false>(a, device, s);
-    case 48: return launch_cgne_t<48, false>(a, device, s);
-    case 64: return launch_cgne_t<64, false>(a, device, s);
+    case 16: return launch_cgne_t<16, false>(a, device, s, sms_use);
+    case 24: return launch_cgne_t<24, false>(a, device, s, sms_use);
+    case 32: return launch_cgne_t<32, false>(a, device, s, sms_use);
+    case 48: return launch_cgne_t<48, false>(a, device, s, sms_use);
+    case 64: return launch_cgne_t<64, false>(a, device, s, sms_use);
     default: return false;
   }
 }

@@ -391,17 +391,19 @@ __global__ void k_sum_planes(const double2* __restrict__ Y, double* __restrict__
 }
 
 template <int NC, bool M3>
-bool launch_t(const Args& args, int device, cudaStream_t s) {
-  static int cached_grid[64] = {0};
-  int& grid = cached_grid[device & 63];
-  if (grid == 0) {
-    int occ = 0, sms = 0, coop = 0;
+bool launch_t(const Args& args, int device, cudaStream_t s, int sms_use) {
+  static int cached_sms[64] = {0};
+  int& sms = cached_sms[device & 63];
+  if (sms == 0) {
+    int occ = 0, coop = 0, n = 0;
     SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne64<NC, M3>, kThreads, 0));
-    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    SW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device));
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
-    if (!coop || occ < 1 || sms > kReduceBlocks) return false;
-    grid = sms;  // one CTA of 16 warps per SM (partials hold 2 x kReduceBlocks)
+    if (!coop || occ < 1 || n > kReduceBlocks) return false;
+    sms = n;
   }
+  // one CTA of 16 warps per SM it may use (partials hold 2 x kReduceBlocks)
+  const int grid = sms_use < sms ? (sms_use > 0 ? sms_use : 1) : sms;
   Args a = args;
   void* params[] = {&a};
   SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne64<NC, M3>, dim3(grid),
@@ -411,8 +413,9 @@ bool launch_t(const Args& args, int device, cudaStream_t s) {
 }
 
 template <int NC>
-bool launch_v(const Args& a, int variant, int device, cudaStream_t s) {
-  return variant == 1 ? launch_t<NC, true>(a, device, s) : launch_t<NC, false>(a, device, s);
+bool launch_v(const Args& a, int variant, int device, cudaStream_t s, int sms_use) {
+  return variant == 1 ? launch_t<NC, true>(a, device, s, sms_use)
+                      : launch_t<NC, false>(a, device, s, sms_use);
 }
 
 }  // namespace
@@ -439,7 +442,7 @@ float cgne64_l2_fraction(long bytes, int device) {
 bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const double* Ys,
                    const double2* b, double2* x, double2* r, double2* p, double* v4,
                    double* partials, unsigned* bar, int* status, int maxit, double tol,
-                   int device, cudaStream_t s, int stall_test) {
+                   int device, cudaStream_t s, int stall_test, int sms_use) {
   if (!cgne64_supported(g.nc)) return false;
   SW_REQUIRE(((size_t)v4 & 31) == 0, SW_ERR_ARG, "CGNE vector forms need 32-byte alignment");
   SW_REQUIRE(variant == 0 || Ys, SW_ERR_ARG, "three-FMA CGNE needs the sum plane");
@@ -450,11 +453,11 @@ bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const dou
   Args a{Y, Ys, b, x, r, p, reinterpret_cast<V4*>(v4), reinterpret_cast<V4*>(v4) + n, partials,
          bar, status, g.E0, g.E1, maxit, tol, stall_test, cgne64_l2_fraction(ybytes, device)};
   switch (g.nc) {
-    case 16: return launch_v<16>(a, variant, device, s);
-    case 24: return launch_v<24>(a, variant, device, s);
-    case 32: return launch_v<32>(a, variant, device, s);
-    case 48: return launch_v<48>(a, variant, device, s);
-    case 64: return launch_v<64>(a, variant, device, s);
+    case 16: return launch_v<16>(a, variant, device, s, sms_use);
+    case 24: return launch_v<24>(a, variant, device, s, sms_use);
+    case 32: return launch_v<32>(a, variant, device, s, sms_use);
+    case 48: return launch_v<48>(a, variant, device, s, sms_use);
+    case 64: return launch_v<64>(a, variant, device, s, sms_use);
     default: return false;
   }
 }

@@ -169,23 +169,62 @@ __global__ void k_restrict_fine(const double2* __restrict__ P, const double2* __
   out[(long)A * 2 * nv + t] = acc;
 }
 
+// Aggregate A and chirality half c (0: eps = +1, 1: eps = -1) of the fine dof
+// at parity-split position h (level-1 aggregates of a0 x a1 KD blocks).
+__device__ __forceinline__ void fine_dof_map(int h, int L0, int L1, int a0, int a1, int& A,
+                                             int& c) {
+  int x0, x1;
+  ps_coords(h, L0, L0 * L1, x0, x1);
+  const int E0 = L0 / (2 * a0);
+  A = x0 / (2 * a0) + E0 * (x1 / (2 * a1));
+  const int k = (x0 & 1) | ((x1 & 1) << 1);
+  c = (k == 1 || k == 2);
+}
+// Aggregate A and chirality half c (0: sigma3 = +1, 1: sigma3 = -1) of dof
+// X nc + k of a coarse level (aggregates of b0 x b1 coarse sites).
+__device__ __forceinline__ void coarse_dof_map(long dof, int E0, int nc, int b0, int b1, int& A,
+                                               int& c) {
+  const int X = (int)(dof / nc), k = (int)(dof - (long)X * nc);
+  const int X0 = X % E0, X1 = X / E0;
+  A = X0 / b0 + (E0 / b0) * (X1 / b1);
+  c = k >= nc / 2;
+}
+
 __global__ void k_prolong_fine(const double2* __restrict__ P, const double2* __restrict__ ehat,
                                double2* __restrict__ e_e, int L0, int L1, int a0, int a1, int nv,
                                int full) {
   int N = L0 * L1;
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= (full ? N : N / 2)) return;
-  int x0, x1;
-  ps_coords(h, L0, N, x0, x1);
-  int E0 = L0 / (2 * a0);
-  int A = x0 / (2 * a0) + E0 * (x1 / (2 * a1));
-  int k = (x0 & 1) | ((x1 & 1) << 1);
-  int c = (k == 1 || k == 2);
+  int A, c;
+  fine_dof_map(h, L0, L1, a0, a1, A, c);
   const double2* p = P + (long)h * nv;
   const double2* eh = ehat + (long)A * 2 * nv + c * nv;
   double2 acc = make_double2(0.0, 0.0);
   for (int i = 0; i < nv; ++i) cfma(acc, p[i], eh[i]);
   e_e[h] = acc;
+}
+
+// Aggregate and chirality (+1 / -1) of every dof of a level, from the index
+// maps of the prolongation kernels (test export): level 1 in lexicographic
+// site order, coarser levels in dof order X nc + k.
+__global__ void k_level_maps_fine(int* __restrict__ agg, int* __restrict__ chir, int L0, int L1,
+                                  int a0, int a1) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= L0 * L1) return;
+  int A, c;
+  fine_dof_map(ps_index(s % L0, s / L0, L0, L0 * L1), L0, L1, a0, a1, A, c);
+  agg[s] = A;
+  chir[s] = c ? -1 : 1;
+}
+__global__ void k_level_maps_coarse(int* __restrict__ agg, int* __restrict__ chir, int E0, int E1,
+                                    int nc, int b0, int b1) {
+  long dof = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (dof >= (long)E0 * E1 * nc) return;
+  int A, c;
+  coarse_dof_map(dof, E0, nc, b0, b1, A, c);
+  agg[dof] = A;
+  chir[dof] = c ? -1 : 1;
 }
 
 // Level >= 2 transfer: chirality sigma3 = + for k < nc/2, - otherwise.
@@ -216,10 +255,8 @@ __global__ void k_prolong_coarse(const double2* __restrict__ P, const double2* _
                                  int nv) {
   long dof = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (dof >= (long)E0 * E1 * nc) return;
-  int X = (int)(dof / nc), k = (int)(dof - (long)X * nc);
-  int X0 = X % E0, X1 = X / E0;
-  int A = X0 / b0 + (E0 / b0) * (X1 / b1);
-  int c = k >= nc / 2;
+  int A, c;
+  coarse_dof_map(dof, E0, nc, b0, b1, A, c);
   const double2* p = P + dof * nv;
   const double2* eh = ehat + (long)A * 2 * nv + c * nv;
   double2 acc = make_double2(0.0, 0.0);
@@ -649,5 +686,17 @@ void launch_block_ortho_coarse(const CoarseGeom& g, int b0, int b1, int nv, cons
 }
 void launch_gaussian(uint64_t seed, long n, double2* out, cudaStream_t s) {
   k_gaussian<<<cdiv(n, 256), 256, 0, s>>>(seed, n, out);
+  SW_LAUNCH_CHECK();
+}
+
+void launch_level_maps_fine(const sw_gauge* g, int a0, int a1, int* agg, int* chir,
+                            cudaStream_t s) {
+  k_level_maps_fine<<<cdiv(g->N, 128), 128, 0, s>>>(agg, chir, g->L0, g->L1, a0, a1);
+  SW_LAUNCH_CHECK();
+}
+void launch_level_maps_coarse(const CoarseGeom& g, int b0, int b1, int* agg, int* chir,
+                              cudaStream_t s) {
+  long n = (long)g.E0 * g.E1 * g.nc;
+  k_level_maps_coarse<<<cdiv(n, 128), 128, 0, s>>>(agg, chir, g.E0, g.E1, g.nc, b0, b1);
   SW_LAUNCH_CHECK();
 }

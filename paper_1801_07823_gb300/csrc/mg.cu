@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -247,12 +248,50 @@ static GcrResult fgcr(sw_mg* mg, int l, const double2* b, double2* x, double tol
 // sequential loop: every kernel after the stopping iteration is a no-op.
 constexpr int kIterBatch = 8;
 
-// One persistent (cooperative) kernel at a time per process: two cooperative
-// grids launched from different streams could each hold part of the SMs
-// while waiting at a grid barrier for their own remaining CTAs.
-static std::mutex g_persistent_mutex;
+// SMs that persistent (cooperative) kernels of this process hold, per device.
+// A persistent launch takes its context's share of the SMs (sw_context_set_
+// sm_share; all of them by default) and waits while the kernels of other
+// contexts hold too many for it to fit beside them.  Grids whose shares add
+// up to at most the SM count run concurrently (one CTA per SM each); others
+// run one after the other, so no cooperative grid waits at a barrier for CTAs
+// that cannot become resident.
+class SmLease {
+ public:
+  explicit SmLease(sw_ctx* c) : dev_(c->device & 63) {
+    int total = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&total, cudaDevAttrMultiProcessorCount, c->device));
+    n_ = (int)((long)total * c->sm_num / (c->sm_den > 0 ? c->sm_den : 1));
+    n_ = n_ < 1 ? 1 : (n_ > total ? total : n_);
+    std::unique_lock<std::mutex> lk(mu());
+    cv().wait(lk, [&] { return used()[dev_] + n_ <= total; });
+    used()[dev_] += n_;
+  }
+  ~SmLease() {
+    {
+      std::lock_guard<std::mutex> lk(mu());
+      used()[dev_] -= n_;
+    }
+    cv().notify_all();
+  }
+  int sms() const { return n_; }
 
-// Autotuner records, keyed by (device, nc, batch width, coarse sites): for the
+ private:
+  static std::mutex& mu() {
+    static std::mutex m;
+    return m;
+  }
+  static std::condition_variable& cv() {
+    static std::condition_variable v;
+    return v;
+  }
+  static int* used() {
+    static int u[64] = {0};
+    return u;
+  }
+  int dev_, n_ = 0;
+};
+
+// Autotuner records, keyed by (device, nc, batch width, coarse sites, SMs used): for the
 // batched tensor-core kernel the pipeline depth, for the single-right-hand-side
 // FP64 kernel (width 1) its variant (0: four-FMA, 1: three-FMA products).
 struct TuneRec {
@@ -260,14 +299,16 @@ struct TuneRec {
   double us_per_iter;
 };
 static std::mutex g_tune_mutex;
-static std::map<std::tuple<int, int, int, int>, TuneRec> g_tune;
+static std::map<std::tuple<int, int, int, int, int>, TuneRec> g_tune;  // + SMs used
 
 // Variant of the FP64 coarsest CGNE for this level, chosen on first use per
 // (device, nc, sites) by timing each for a few iterations on the call's own
 // data (the real solve then starts from scratch).
-static int cgne64_variant(sw_mg* mg, MgLevel& L, const double2* b, double2* x) {
+static int cgne64_variant(sw_mg* mg, MgLevel& L, const double2* b, double2* x, int sms) {
   sw_ctx* c = mg->ctx;
-  const auto key = std::make_tuple(c->device, L.nc, 1, L.E0 * L.E1);
+  const char* force = std::getenv("SW_CGNE64");  // "0" or "1": skip the timing, use this one
+  if (force && (force[0] == '0' || force[0] == '1') && !force[1]) return force[0] - '0';
+  const auto key = std::make_tuple(c->device, L.nc, 1, L.E0 * L.E1, sms);
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tune.find(key);
@@ -284,7 +325,7 @@ static int cgne64_variant(sw_mg* mg, MgLevel& L, const double2* b, double2* x) {
       SW_CUDA(cudaEventRecord(e0, c->stream));
       bool ran = launch_cgne64(CoarseGeom{L.E0, L.E1, L.nc}, v, L.Y, L.Ys, b, x, L.gr, L.cp,
                                L.c4, c->partials, c->bar, c->cgstat, kTuneIters, 0.0, c->device,
-                               c->stream);
+                               c->stream, 0, sms);
       SW_CUDA(cudaEventRecord(e1, c->stream));
       SW_CUDA(cudaEventSynchronize(e1));
       SW_REQUIRE(ran, SW_ERR_ARG, "FP64 coarsest CGNE has no variant for this shape");
@@ -310,17 +351,18 @@ static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
   MgLevel& L = mg->lev[l];
   long n = level_len(mg, l);
   if (mg->persistent_cgne) {
-    std::lock_guard<std::mutex> lock(g_persistent_mutex);  // held until the kernel has finished
+    SmLease lease(c);  // held until the kernel has finished
     int tk = -1;
     const char* dfenv = std::getenv("SW_COARSEST_DF64");
     bool df = mg->mixed && L.Ydf && (!(L.Ys && L.c4) || (dfenv && dfenv[0] == '1'));
     bool ran;
     if (!df && L.Ys && L.c4) {
-      const int v = cgne64_variant(mg, L, b, x);
+      const int v = cgne64_variant(mg, L, b, x, lease.sms());
       tk = timing_begin(c, kCatCgne);  // the bracket covers the solve, not the tuning
       ran = launch_cgne64(CoarseGeom{L.E0, L.E1, L.nc}, v, L.Y, L.Ys, b, x, L.gr, L.cp, L.c4,
                           c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
-                          mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
+                          mg->p.coarsest_tol, c->device, c->stream, mg->stall_test,
+                          lease.sms());
     }
     else {
       tk = timing_begin(c, kCatCgne);
@@ -329,7 +371,8 @@ static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
                                    df ? 1 : 0, b, x, L.gr, L.cp, L.cdf,
                                    L.cdf ? L.cdf + L.ndof : nullptr,
                                    c->partials, c->bar, c->cgstat, mg->p.coarsest_maxiter,
-                                   mg->p.coarsest_tol, c->device, c->stream, mg->stall_test);
+                                   mg->p.coarsest_tol, c->device, c->stream, mg->stall_test,
+                                   lease.sms());
     }
     timing_end(c, tk);
     if (ran) {
@@ -854,11 +897,14 @@ SetResult fgcr_b(sw_mg* mg, int l, const Set& set, const std::vector<const doubl
 // (device, nc, width, coarse sites) by timing each candidate for a few
 // iterations on the call's own data (the real solve then starts from scratch).
 
-int tc_stages(sw_mg* mg, const MgLevel& L, int nb, double2* const* bptr, double2* const* xptr) {
+int tc_stages(sw_mg* mg, const MgLevel& L, int nb, double2* const* bptr, double2* const* xptr,
+              int sms) {
   sw_ctx* c = mg->ctx;
   BatchWs& B = mg->batch;
   const int K = tc_width(nb);
-  const auto key = std::make_tuple(c->device, L.nc, K, L.E0 * L.E1);
+  const bool f32 = mg->p.batch_iterates == SW_PREC_FP32;
+  // batch widths of FP32-iterate runs are recorded as 100 + K
+  const auto key = std::make_tuple(c->device, L.nc, f32 ? 100 + K : K, L.E0 * L.E1, sms);
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tune.find(key);
@@ -876,9 +922,9 @@ int tc_stages(sw_mg* mg, const MgLevel& L, int nb, double2* const* bptr, double2
     float tot = 0.f;
     for (int rep = 0; rep <= kReps; ++rep) {  // rep 0 is a warm-up
       SW_CUDA(cudaEventRecord(e0, c->stream));
-      bool ran = launch_cgne_tc(CoarseGeom{L.E0, L.E1, L.nc}, opts[k], B.At, B.Ad, nb, bptr,
+      bool ran = launch_cgne_tc(CoarseGeom{L.E0, L.E1, L.nc}, opts[k], f32, B.At, B.Ad, nb, bptr,
                                 xptr, B.X, B.R, B.P, B.Rt, B.Pt, B.partials, B.bar, B.status,
-                                kTuneIters, 0.0, c->device, c->stream, 0);
+                                kTuneIters, 0.0, c->device, c->stream, 0, sms);
       SW_CUDA(cudaEventRecord(e1, c->stream));
       SW_CUDA(cudaEventSynchronize(e1));
       SW_REQUIRE(ran, SW_ERR_ARG, "tensor-core batched CGNE has no variant for this shape");
@@ -906,6 +952,7 @@ void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc, int stall = 0) 
   BatchWs& B = mg->batch;
   const int nb = (int)set.size();
   const bool tc = tc_supported(L.nc) && !B.Yf;
+  const bool f32 = mg->p.batch_iterates == SW_PREC_FP32;
   double2* hp[2 * kMaxBatch] = {nullptr};
   for (int i = 0; i < nb; ++i) {
     hp[i] = B.lv[l][set[i]].rhs;
@@ -913,7 +960,7 @@ void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc, int stall = 0) 
   }
   SW_CUDA(cudaMemcpyAsync(B.dptr, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));
   SW_CUDA(cudaStreamSynchronize(c->stream));  // hp is a host stack array
-  std::lock_guard<std::mutex> lock(g_persistent_mutex);
+  SmLease lease(c);
   std::vector<int> its(nb, 0);
   // the CUDA-core FP32 kernel (SW_BATCH_FP32=1) takes at most 16 at a time
   const int chunk = tc ? kMaxBatch : 16;
@@ -922,18 +969,18 @@ void cgne_b(sw_mg* mg, int l, const Set& set, BatchCounters& bc, int stall = 0) 
     bool ran;
     int tk;
     if (tc) {
-      const int S = tc_stages(mg, L, m, B.dptr + i0, B.dptr + kMaxBatch + i0);
+      const int S = tc_stages(mg, L, m, B.dptr + i0, B.dptr + kMaxBatch + i0, lease.sms());
       tk = timing_begin(c, kCatCgne);
-      ran = launch_cgne_tc(CoarseGeom{L.E0, L.E1, L.nc}, S, B.At, B.Ad, m, B.dptr + i0,
+      ran = launch_cgne_tc(CoarseGeom{L.E0, L.E1, L.nc}, S, f32, B.At, B.Ad, m, B.dptr + i0,
                            B.dptr + kMaxBatch + i0, B.X, B.R, B.P, B.Rt, B.Pt, B.partials,
                            B.bar, B.status, mg->p.coarsest_maxiter, mg->p.coarsest_tol,
-                           c->device, c->stream, stall);
+                           c->device, c->stream, stall, lease.sms());
     } else {
       tk = timing_begin(c, kCatCgne);
       ran = launch_cgne_batch(CoarseGeom{L.E0, L.E1, L.nc}, B.Yf, B.Yd, m, B.dptr + i0,
                               B.dptr + kMaxBatch + i0, B.X, B.R, B.P, B.Rf, B.Pf, B.partials,
                               B.bar, B.status, mg->p.coarsest_maxiter, mg->p.coarsest_tol,
-                              c->device, c->stream);
+                              c->device, c->stream, lease.sms());
     }
     timing_end(c, tk);
     if (!ran)

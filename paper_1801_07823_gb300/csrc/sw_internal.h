@@ -112,6 +112,7 @@ struct sw_ctx {
   unsigned* bar = nullptr;       // grid-barrier state of persistent kernels (2 words)
   int* cgstat = nullptr;         // status words of the persistent CGNE (3 ints)
   double2* h_slots = nullptr;    // pinned host mirror
+  int sm_num = 1, sm_den = 1;    // share of the SMs its persistent kernels may hold
 };
 
 struct sw_gauge {
@@ -256,7 +257,8 @@ void launch_coarse_apply(const CoarseGeom& g, const double2* Y, int dagger, cons
 bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const double2* b,
                             double2* x, double2* r, double2* p, float4* rdf, float4* pdf,
                             double* partials, unsigned* bar, int* status, int maxit, double tol,
-                            int device, cudaStream_t s, int stall_test = 0);
+                            int device, cudaStream_t s, int stall_test = 0,
+                            int sms_use = 1 << 30);
 
 // FP64 coarsest CGNE in one persistent kernel (cgne64.cu).  variant 1: three
 // real FMAs per complex product, reading Ys = Re + Im of every entry of Y
@@ -268,7 +270,7 @@ void launch_sum_planes(const double2* Y, double* Ys, long n, cudaStream_t s);
 bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const double* Ys,
                    const double2* b, double2* x, double2* r, double2* p, double* v4,
                    double* partials, unsigned* bar, int* status, int maxit, double tol,
-                   int device, cudaStream_t s, int stall_test = 0);
+                   int device, cudaStream_t s, int stall_test = 0, int sms_use = 1 << 30);
 
 // Batched coarsest CGNE (batch_cgne.cu): nb <= 16 right-hand sides, FP32
 // forward stencil Yf and adjoint stencil Yd (launch_adjoint_f32), FP64
@@ -280,23 +282,25 @@ int cgne_batch_width(int nb);
 bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, int nb,
                        const double2* const* b, double2* const* x, double2* X, double2* R,
                        double2* P, float2* Rf, float2* Pf, double* partials, unsigned* bar,
-                       int* status, int maxit, double tol, int device, cudaStream_t s);
+                       int* status, int maxit, double tol, int device, cudaStream_t s,
+                       int sms_use = 1 << 30);
 // Batched coarsest CGNE on the tensor cores (batch_tc.cu): nb <= 64
 // right-hand sides padded to the width tc_width(nb) in {8, 16, 32, 64}.
 // At / Ad: stacked TF32 tiles (launch_stack_tiles, tc_tile_floats(nc) floats
 // per (site, direction)); Rt / Pt: sites x 2 K x nc floats of scratch; X, R, P:
-// [n][K] double2; partials: 2 K SMs doubles; status: 2 + 64 ints ([0] wait
-// timeout or misaligned buffer, [1] non-finite, [2 + r] iterations).
-// stages: pipeline depth, one of tc_stage_options(nc, K).
+// [n][K] double2 (float2 with f32: FP32 iterates); partials: 2 K SMs doubles;
+// status: 2 + 64 ints ([0] wait timeout or misaligned buffer, [1] non-finite,
+// [2 + r] iterations).  stages: pipeline depth, one of tc_stage_options(nc, K).
 int tc_width(int nb);
 bool tc_supported(int nc);
 long tc_tile_floats(int nc);
 int tc_stage_options(int nc, int K, int* out);
 void launch_stack_tiles(const CoarseGeom& g, const double2* Y, float* T, int adj, cudaStream_t s);
-bool launch_cgne_tc(const CoarseGeom& g, int stages, const float* At, const float* Ad, int nb,
-                    const double2* const* b, double2* const* x, double2* X, double2* R,
+bool launch_cgne_tc(const CoarseGeom& g, int stages, bool f32, const float* At, const float* Ad,
+                    int nb, const double2* const* b, double2* const* x, double2* X, double2* R,
                     double2* P, float* Rt, float* Pt, double* partials, unsigned* bar,
-                    int* status, int maxit, double tol, int device, cudaStream_t s, int stall);
+                    int* status, int maxit, double tol, int device, cudaStream_t s, int stall,
+                    int sms_use = 1 << 30);
 // Yd[X][d] = Y[nb(X, d)][opp(d)]^dag in FP32, every block column-major like Y.
 void launch_adjoint_f32(const CoarseGeom& g, const double2* Y, float2* Yd, cudaStream_t s);
 
@@ -324,6 +328,11 @@ void launch_restrict_coarse(const CoarseGeom& g, int b0, int b1, int nv, const d
                             const double2* r, double2* out, cudaStream_t s);
 void launch_prolong_coarse(const CoarseGeom& g, int b0, int b1, int nv, const double2* P,
                            const double2* ehat, double2* e, cudaStream_t s);
+// Aggregate / chirality maps of a level from the transfer kernels' index maps.
+void launch_level_maps_fine(const sw_gauge* g, int a0, int a1, int* agg, int* chir,
+                            cudaStream_t s);
+void launch_level_maps_coarse(const CoarseGeom& g, int b0, int b1, int* agg, int* chir,
+                              cudaStream_t s);
 // Galerkin builds.
 void launch_build_W(const sw_gauge* g, int nv, const double2* binv, const double2* P,
                     double2* Wv, cudaStream_t s);

@@ -34,7 +34,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import SW_MG_MIXED, sw_context_create, sw_gauge_load, sw_mg_params_default, sw_mg_setup
-from . import sw_mg_solve, sw_mg_solve_batch
+from . import sw_context_set_sm_share, sw_mg_solve, sw_mg_solve_batch
 
 
 def hierarchy_bytes(L: int, blocks, nvec, mixed: bool, outer_restart: int = 32,
@@ -54,6 +54,8 @@ def hierarchy_bytes(L: int, blocks, nvec, mixed: bool, outer_restart: int = 32,
         last = l == len(nvec) - 1
         ysz = sites * 5 * nc * nc
         b += ysz * 16                              # Y (FP64)
+        if last:
+            b += ysz * 8 + sites * nc * 64         # sum plane and vector forms of its FP64 CGNE
         if mixed:
             b += ysz * (16 if last else 4) + sites * 5 * 4
         nb = 0 if last else inter_restart
@@ -114,11 +116,19 @@ class Server:
 
     gauges: list of (theta [2, L, L], label).  masses: the mass grid.
     workers: number of concurrent streams.  hbm_budget: bytes that resident
-    hierarchies may use in total."""
+    hierarchies may use in total.  sm_share: (num, den) share of the SMs each
+    worker's persistent coarsest kernels hold (default 1/workers, so that the
+    coarsest solves of all workers can run at the same time); a request's
+    result depends on the share, not on the other requests in flight.
+    affinity: every hierarchy (gauge field, mass) belongs to one worker (dealt
+    round-robin in order of first use), which serves all of its requests, so
+    each hierarchy is set up once and its queued requests meet in one queue
+    for batching; without it any free worker takes any request and builds the
+    hierarchies it needs itself."""
 
     def __init__(self, gauges, masses, workers=2, hbm_budget=40 << 30, tol=1e-10, mixed=True,
                  blocks=((4, 4), (2, 2)), nvec=(24, 32), params=None, device=0, psi0_fn=None,
-                 batch_max=1):
+                 batch_max=1, sm_share=None, affinity=False):
         import torch
         if int(batch_max) > 1 and not mixed:
             raise ValueError("batch_max > 1 needs mixed=True: sw_mg_solve_batch batches the "
@@ -133,7 +143,9 @@ class Server:
         self.params = params or {}
         self.budget = hbm_budget
         self.psi0_fn = psi0_fn
-        self.batch_max = max(1, min(16, int(batch_max)))
+        self.batch_max = max(1, min(64, int(batch_max)))
+        self.affinity = affinity
+        self.owner = {}
         self.lock = threading.Condition()
         self.queue: list[Request] = []
         self.done: list[Request] = []
@@ -144,6 +156,8 @@ class Server:
             with torch.cuda.device(device):
                 stream = torch.cuda.Stream()
             ctx = sw_context_create(device, stream.cuda_stream)
+            share = sm_share or (1, workers)
+            sw_context_set_sm_share(ctx, share[0], share[1])
             gh = [sw_gauge_load(ctx, th) for th, _ in gauges]
             self.workers.append(dict(id=w, stream=stream, ctx=ctx, gauges=gh, cache={},
                                      busy=False, thread=None))
@@ -156,9 +170,33 @@ class Server:
     def snap_mass(self, m: float) -> float:
         return float(self.masses[np.argmin(np.abs(np.log(self.masses) - np.log(m)))])
 
+    def _own(self, key):
+        """Worker that owns hierarchy `key` under affinity (lock held)."""
+        if key not in self.owner:
+            self.owner[key] = len(self.owner) % len(self.workers)
+        return self.owner[key]
+
+    def prewarm(self, keys):
+        """Builds the hierarchies of (gauge, mass) keys before requests arrive
+        (on their owners under affinity, else on every worker) and returns the
+        wall time it took."""
+        t0 = time.perf_counter()
+        jobs = []
+        for wk in self.workers:
+            mine = [k for k in keys if not self.affinity or self._own(k) == wk["id"]]
+            jobs.append(threading.Thread(target=lambda w=wk, ks=mine: [self._hierarchy(w, k)
+                                                                        for k in ks]))
+        for j in jobs:
+            j.start()
+        for j in jobs:
+            j.join()
+        return time.perf_counter() - t0
+
     def submit(self, rid: int, gauge: int, mass: float, b: np.ndarray) -> Request:
         r = Request(time.perf_counter(), rid, gauge, self.snap_mass(mass), b)
         with self.lock:
+            if self.affinity:
+                self._own((r.gauge, r.mass))
             heapq.heappush(self.queue, r)
             self.lock.notify_all()
         return r
@@ -202,6 +240,8 @@ class Server:
         hierarchy it already holds, else the earliest one whose hierarchy fits
         the HBM budget after evicting this worker's least recently used ones."""
         order = sorted(self.queue)
+        if self.affinity:
+            order = [r for r in order if self.owner[(r.gauge, r.mass)] == wk["id"]]
         for r in order:
             if (r.gauge, r.mass) in wk["cache"]:
                 return r, 0
@@ -215,6 +255,28 @@ class Server:
             if self.used + need <= self.budget:
                 return r, need
         return None, 0
+
+    def _hierarchy(self, wk, key, need=None):
+        """Sets up (once) the hierarchy `key` on worker wk's stream and context."""
+        if key in wk["cache"]:
+            return wk["cache"][key]
+        if need is None:  # prewarm: account for it here
+            need = self._footprint(key[0])
+            with self.lock:
+                self.used += need
+        gauge, mass = key
+        p = sw_mg_params_default()
+        for k, v in self.params.items():
+            setattr(p, k, v)
+        if self.mixed:
+            p.precision = SW_MG_MIXED
+        L = self.gauges[gauge][0].shape[-1]
+        psi0 = self.psi0_fn(L) if self.psi0_fn else None
+        with self.torch.cuda.stream(wk["stream"]):
+            mg = sw_mg_setup(wk["gauges"][gauge], mass, len(self.nvec) + 1, self.blocks,
+                             self.nvec, params=p, psi0=psi0)
+        wk["cache"][key] = dict(mg=mg, bytes=need, last=time.perf_counter())
+        return wk["cache"][key]
 
     def _run(self, wk):
         torch = self.torch
@@ -241,21 +303,12 @@ class Server:
                 with torch.cuda.stream(wk["stream"]):
                     key = (r.gauge, r.mass)
                     if key not in wk["cache"]:
-                        p = sw_mg_params_default()
-                        for k, v in self.params.items():
-                            setattr(p, k, v)
-                        if self.mixed:
-                            p.precision = SW_MG_MIXED
-                        L = self.gauges[r.gauge][0].shape[-1]
-                        psi0 = self.psi0_fn(L) if self.psi0_fn else None
                         try:
-                            mg = sw_mg_setup(wk["gauges"][r.gauge], r.mass, len(self.nvec) + 1,
-                                             self.blocks, self.nvec, params=p, psi0=psi0)
+                            self._hierarchy(wk, key, need)
                         except Exception:
                             with self.lock:
                                 self.used -= need
                             raise
-                        wk["cache"][key] = dict(mg=mg, bytes=need, last=0.0)
                     h = wk["cache"][key]
                     h["last"] = time.perf_counter()
                     if self.batch_max > 1:

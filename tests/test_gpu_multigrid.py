@@ -571,3 +571,91 @@ def test_nan_right_hand_side_is_reported(sw, mixed64):
     b = si.gaussian_complex(7805, L * L)
     st = sw.sw_mg_solve(h64, b, x, 1e-10)
     assert st["converged"] and st["true_resid"] <= 1e-10
+
+
+def test_level_maps_bit_exact(sw, ctx):
+    """The aggregate and chirality maps the transfer kernels use, on a lattice
+    and hierarchy with unequal extents and aggregates (48 x 32, 2 x 4 KD blocks,
+    then 2 x 2 coarse sites), equal the oracle's maps bit for bit: level 1
+    aggregates of KD blocks with chirality eps (Eq. epsilon), level 2 aggregates
+    of coarse sites with chirality sigma3 (+ on the first nvec dof of a site)."""
+    L0, L1 = 48, 32
+    blocks, nvec = [(2, 4), (2, 2)], [2, 3]
+    th = si.heatbath_u1(L0, L1, 6.0, 10, seed=9, device="cpu")
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, 0.1, 3, blocks, nvec, psi0=psi0_arrays(L0, L1, nvec, 3, blocks))
+    agg, chir = sw.sw_mg_level_maps(h, 1)
+    assert np.array_equal(agg, lattice.fine_aggregate(L0, L1, 2, 4))
+    assert np.array_equal(chir, lattice.epsilon(L0, L1))
+    E0, E1, nc = sw.sw_mg_level_info(h, 2)
+    assert (E0, E1, nc) == (12, 4, 4)
+    agg, chir = sw.sw_mg_level_maps(h, 2)
+    assert np.array_equal(agg, np.repeat(lattice.coarse_aggregate(E0, E1, 2, 2), nc))
+    assert np.array_equal(chir, np.tile(np.r_[np.ones(2, int), -np.ones(2, int)], E0 * E1))
+    h.free()
+    g.free()
+
+
+def test_config3_mixed_small_against_oracle(sw, ctx):
+    """Mixed precision on the small plain workload (32^2, beta 3 with 1000
+    sweeps, m 0.01, 2 levels, 4 x 4 aggregates, 8 null vectors from 4 setup
+    passes): single and batched mixed solves reach the 1e-10 true residual, and
+    their solutions are within 1e-8 of the FP64 oracle's own solve (the error a
+    1e-10 residual allows at this condition number)."""
+    cs = SOLVE_CASES[2]
+    L, m, blocks, nvec = cs["L"], cs["m"], cs["blocks"], cs["nvec"]
+    th = si.heatbath_u1(L, L, cs["beta"], cs["sweeps"], seed=1, device="cpu")
+    psi0 = psi0_arrays(L, L, nvec, 2, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    h = sw.sw_mg_setup(g, m, 2, blocks, nvec,
+                       params=params(sw, precision=sw.SW_MG_MIXED, setup_passes=cs["passes"]),
+                       psi0=psi0)
+    H = omg.Hierarchy(th, m, 2, blocks, nvec, [list(a) for a in psi0],
+                      omg.Params(setup_passes=cs["passes"]))
+    D = operators.dirac(th, m)
+    B = np.stack([si.gaussian_complex(8100 + k, L * L) for k in range(4)])
+    X = np.zeros_like(B)
+    sts = sw.sw_mg_solve_batch(h, B, X, 1e-10)
+    for k in range(4):
+        xo, _ = H.solve(B[k], 1e-12)
+        x1 = np.zeros(L * L, dtype=complex)
+        s1 = sw.sw_mg_solve(h, B[k], x1, 1e-10)
+        for x, st in ((x1, s1), (X[k], sts[k])):
+            r = np.linalg.norm(B[k] - D @ x) / np.linalg.norm(B[k])
+            assert st["converged"] and r <= 1e-10, (k, r)
+            assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-8
+    h.free()
+    g.free()
+
+
+def test_config3_mixed_512(sw, ctx):
+    """Mixed precision at 512^2, beta 10 (300 sweeps), m 0.01 with the 3-level
+    hierarchy of the 256^2 workload (4 x 4 then 2 x 2 aggregates, Nv 24/32): the
+    mixed solve and a batch of 8 reach the 1e-10 true residual and agree with
+    the FP64 hierarchy's solve to 1e-8 relative."""
+    L, m, blocks, nvec = 512, 0.01, [(4, 4), (2, 2)], [24, 32]
+    th = si.heatbath_u1(L, L, 10.0, 300, seed=3, device="cuda")
+    psi0 = psi0_arrays(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    from paper_1801_07823_gb300 import presets
+    p64 = presets.make_params(sw, presets.FP64_256)
+    pmx = presets.make_params(sw, presets.FP64_256)
+    pmx.precision = sw.SW_MG_MIXED
+    h64 = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=p64, psi0=psi0)
+    hmx = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=pmx, psi0=psi0)
+    D = operators.dirac(th, m)
+    B = np.stack([si.gaussian_complex(8200 + k, L * L) for k in range(8)])
+    x64 = np.zeros(L * L, dtype=complex)
+    st64 = sw.sw_mg_solve(h64, B[0], x64, 1e-10)
+    xm = np.zeros_like(x64)
+    stm = sw.sw_mg_solve(hmx, B[0], xm, 1e-10)
+    X = np.zeros_like(B)
+    sts = sw.sw_mg_solve_batch(hmx, B, X, 1e-10)
+    for x, st, b in ((x64, st64, B[0]), (xm, stm, B[0]), (X[0], sts[0], B[0]), (X[7], sts[7], B[7])):
+        r = np.linalg.norm(b - D @ x) / np.linalg.norm(b)
+        assert st["converged"] and r <= 1e-10, r
+    for x in (xm, X[0]):
+        assert np.linalg.norm(x - x64) / np.linalg.norm(x64) < 1e-8
+    hmx.free()
+    h64.free()
+    g.free()

@@ -9,7 +9,14 @@ from tests.gpu_helpers import psi0_arrays
 pytestmark = pytest.mark.gpu
 
 
-def test_serving_results_alone_equal_mixed():
+@pytest.mark.parametrize("batch_max", [1, 4])
+def test_serving_results_alone_equal_mixed(batch_max):
+    """Each request's solution is bitwise the same when it is served alone and
+    when it is served among concurrent requests on three workers, with and
+    without batching of queued requests on one hierarchy (mixed precision, so
+    batches use the tensor-core coarsest kernel); every worker holds a third of
+    the SMs for its coarsest kernels in both runs.  With batching, some
+    requests must have been solved in a batch."""
     from paper_1801_07823_gb300 import serve
     from oracle import operators
     gauges = [(si.heatbath_u1(L, L, beta, 200, seed=s, device="cuda"), f"L{L} b{beta}")
@@ -17,27 +24,29 @@ def test_serving_results_alone_equal_mixed():
     masses = [0.01, 0.1]
     rng = np.random.default_rng(7)
     reqs = []
-    for i in range(10):
-        gid = int(rng.integers(len(gauges)))
+    for i in range(14):
+        gid = int(rng.integers(2)) if batch_max > 1 else int(rng.integers(len(gauges)))
         L = gauges[gid][0].shape[-1]
         m = float(np.exp(rng.uniform(np.log(1e-2), np.log(1e-1))))
         reqs.append((gid, m, si.gaussian_complex(500 + i, L * L)))
     psi0 = lambda L: psi0_arrays(L, L, [8, 12], 3, [(4, 4), (2, 2)])
-    kw = dict(nvec=(8, 12), psi0_fn=psi0, hbm_budget=4 << 30, params=dict(outer_maxiter=300))
+    kw = dict(nvec=(8, 12), psi0_fn=psi0, hbm_budget=8 << 30, params=dict(outer_maxiter=300),
+              batch_max=batch_max, sm_share=(1, 3))
     alone = serve.Server(gauges, masses, workers=1, **kw)
-    ref = []
     for i, (gid, m, b) in enumerate(reqs):
         alone.submit(i, gid, m, b)
         alone.drain()
     ref = sorted(alone.done, key=lambda r: r.rid)
     alone.close()
     mix = serve.Server(gauges, masses, workers=3, **kw)
-    got = serve.poisson_stream(mix, reqs, rate=200.0)
+    got = serve.poisson_stream(mix, reqs, rate=400.0)
     summary = serve.latency_summary(got)
     workers_used = {r.worker for r in got}
     mix.close()
     assert summary["all_converged"] and len(got) == len(reqs)
     assert len(workers_used) > 1
+    if batch_max > 1:
+        assert max(r.batch for r in got) > 1
     for a, b in zip(ref, got):
         assert a.rid == b.rid and a.mass == b.mass
         assert np.array_equal(a.x, b.x), a.rid

@@ -78,6 +78,7 @@ def fake(monkeypatch):
     monkeypatch.setattr(serve, "sw_mg_setup", f.mg_setup)
     monkeypatch.setattr(serve, "sw_mg_solve", f.mg_solve)
     monkeypatch.setattr(serve, "sw_mg_solve_batch", f.mg_solve_batch)
+    monkeypatch.setattr(serve, "sw_context_set_sm_share", lambda ctx, n, d: None)
     import torch
     monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: types.SimpleNamespace(cuda_stream=0))
     monkeypatch.setattr(torch.cuda, "device", lambda *a, **k: contextlib.nullcontext())
@@ -187,3 +188,29 @@ def test_batching_on_fp64_hierarchies_is_rejected(fake):
         serve.Server(_gauges(n=1), [1e-2], workers=1, mixed=False, batch_max=4)
     srv = serve.Server(_gauges(n=1), [1e-2], workers=1, mixed=False, batch_max=1)
     srv.close()
+
+
+def test_affinity_sets_up_each_hierarchy_once(fake):
+    """With affinity every (gauge, mass) hierarchy is built by one worker only,
+    all of its requests run there, and prewarm builds them before requests
+    arrive."""
+    gauges = _gauges(n=3)
+    srv = serve.Server(gauges, [1e-2, 1e-1], workers=2, affinity=True, batch_max=4)
+    try:
+        keys = [(g, m) for g in range(3) for m in (1e-2, 1e-1)]
+        srv.prewarm(keys)
+        assert fake.setups == len(keys)
+        rng = np.random.default_rng(3)
+        for i in range(30):
+            gi, m = keys[int(rng.integers(len(keys)))]
+            srv.submit(i, gi, m, np.full(256, float(i + 1), dtype=complex))
+        srv.drain()
+        assert fake.setups == len(keys) and len(srv.done) == 30
+        by_key = {}
+        for r in srv.done:
+            by_key.setdefault((r.gauge, r.mass), set()).add(r.worker)
+            assert np.allclose(r.x, r.b / r.mass)
+        assert all(len(w) == 1 for w in by_key.values())
+        assert len({w for ws in by_key.values() for w in ws}) == 2
+    finally:
+        srv.close()
