@@ -103,6 +103,8 @@ def parse():
     ap.add_argument("--batched-only", type=int, default=0, metavar="K",
                     help="run only K-right-hand-side batched solves on the mixed hierarchy "
                          "(one warm-up and --batch-reps timed batches; for profiling)")
+    ap.add_argument("--batch-f32", action="store_true",
+                    help="with --batched-only: FP32 iterates in the batched coarsest CGNE")
     ap.add_argument("--dslash-only", action="store_true",
                     help="run only the Dslash bandwidth microbenchmark")
     ap.add_argument("--batch-reps", type=int, default=3,
@@ -354,12 +356,12 @@ def coarse_stencil_bandwidth(sw, ctx, L=1024, reps=20):
         sw.sw_set_timing(ctx, True)
         for _ in range(reps):
             sw.sw_mg_apply_level(h, 2, prec, 0, v, w)
-        cnt, ms = sw.sw_kernel_times(ctx, 7)[1]
+        ms = sw.sw_kernel_times(ctx, 7)[1][1]  # event-bracketed ms of the reps applications
         sw.sw_set_timing(ctx, False)
-        t = ms / 1e3 / max(cnt, 1)
+        t = ms / 1e3 / reps
         byt = (5 * nc * nc * pb + extra + 2 * nc * 16) * e0 * e1
         out[name] = {"GB/s": byt / t / 1e9, "frac_of_hbm": byt / t / 1e9 / HBM_PEAK_GBS,
-                     "us": t * 1e6, "bytes_per_apply": byt, "applications": cnt}
+                     "us": t * 1e6, "bytes_per_apply": byt, "applications": reps}
     h.free()
     g.free()
     return out
@@ -388,11 +390,14 @@ def serving_measurement(nreq, seed=11, rate=4.0, workers=2, batch_max=8, mixed=T
         m = float(np.exp(rng.uniform(np.log(1e-3), np.log(1e-1))))
         reqs.append((gid, m, si.gaussian_complex(2000 + i, L * L)))
     nv, blocks = [24, 32], [(4, 4), (2, 2)]
-    psi0_fn = lambda L: si.null_vector_guesses(L, L, nv, 3, blocks)
+    # 512^2 and up: one more level (2 x 2, 32 vectors), so that the coarsest grid
+    # stays 16^2 x 64 dof as at 256^2 (Sec. IV: the recursion extends)
+    cfg = lambda L: ((blocks + [(2, 2)], nv + [32]) if L >= 512 else (blocks, nv))
+    psi0_fn = lambda L, b, n: si.null_vector_guesses(L, L, n, len(n) + 1, b)
     srv = serve.Server(gauges, SERVING_MASSES, workers=workers, hbm_budget=160 << 30,
                        nvec=tuple(nv), blocks=blocks, mixed=mixed, psi0_fn=psi0_fn,
                        params=dict(outer_maxiter=400, coarsest_maxiter=2048),
-                       batch_max=batch_max, affinity=True)
+                       batch_max=batch_max, affinity=True, hier_cfg=cfg)
     keys = sorted({(g, srv.snap_mass(m)) for g, m, _ in reqs})
     setup_s = srv.prewarm(keys)
     done = serve.poisson_stream(srv, reqs, rate=rate, seed=seed)
@@ -404,9 +409,13 @@ def serving_measurement(nreq, seed=11, rate=4.0, workers=2, batch_max=8, mixed=T
                        f"{{1e-3, 1e-2, 1e-1}}; Nv 24/32; {workers} worker streams with "
                        f"hierarchy affinity; batch_max {batch_max}; "
                        f"{'mixed precision' if mixed else 'FP64'}; tol 1e-10; hierarchies set "
-                       "up before the stream")
+                       "up before the stream; 512^2 hierarchies with a fourth level (2x2, Nv 32)")
     out["hierarchies"] = len(keys)
     out["setup_s"] = setup_s
+    out["per_request"] = [[r.rid, fields[r.gauge][0], fields[r.gauge][1], r.mass, r.batch,
+                           round(r.finish - r.arrival, 3), round(r.finish - r.start, 3),
+                           int(bool(r.stats.get("converged"))), r.stats.get("outer_iters"),
+                           r.stats.get("error", "")] for r in done]
     out["by_size"] = {str(L): float(np.percentile([r.finish - r.arrival for r in done
                                                    if fields[r.gauge][0] == L], 50))
                       for L in sorted({L for L, _ in fields})
@@ -629,16 +638,22 @@ def run_native(args, rank, world, local):
     shapes = {l: sw.sw_mg_level_info(h, l + 1) for l in (1, 2)}
     cand = {c: ktimes[c][1] for c in (1, 2, 5)}
     best = max(cand, key=cand.get)
+    variant = None
     if best == 5:
         e0, e1, nc = shapes[2]
         iters = ktimes[6][0]
         n_l, ms_l = ktimes[5]
+        # product form the FP64 kernel's autotuner chose (0: four FMAs, 1: three)
+        ch = [e for e in sw.sw_autotune_entries() if e[1] == 1 and e[0] == nc and e[2] == e0 * e1]
+        variant = ch[0][3] if ch else None
         per_apply_flop = 8.0 * 5 * nc * nc * e0 * e1
         flop = per_apply_flop * 2 * iters / max(n_l, 1)      # per launch
-        byt = 16.0 * (5 * nc * nc + 2 * nc) * e0 * e1 * 2 * iters / max(n_l, 1)
-        kname = (f"k_cgne<{nc}> (persistent coarsest CGNE, {e0}x{e1} sites, {nc}x{nc} complex128 "
-                 f"blocks, {iters / max(n_l, 1):.0f} iterations = {2 * iters / max(n_l, 1):.0f} "
-                 f"stencil applications per launch)")
+        ybytes = (24.0 if variant == 1 else 16.0) * 5 * nc * nc * e0 * e1
+        byt = (ybytes + 16.0 * 2 * nc * e0 * e1) * 2 * iters / max(n_l, 1)
+        kname = (f"k_cgne64<{nc}, {'three' if variant == 1 else 'four'}-FMA products> "
+                 f"(persistent FP64 coarsest CGNE, {e0}x{e1} sites, {nc}x{nc} complex128 blocks, "
+                 f"{iters / max(n_l, 1):.0f} iterations = {2 * iters / max(n_l, 1):.0f} stencil "
+                 f"applications per launch)")
     else:
         e0, e1, nc = shapes[best]
         n_l, ms_l = ktimes[best]
@@ -649,14 +664,19 @@ def run_native(args, rank, world, local):
     achieved = flop / dur / 1e12
     traffic = None
     if best == 5:
-        per_iter = _profiled_traffic("k_cgne_fp64_256.md", "paper_1801_07823_gb300/csrc/cgne.cu",
+        per_iter = _profiled_traffic("k_cgne64_fp64_256.md", "paper_1801_07823_gb300/csrc/cgne64.cu",
                                      "dram_bytes_per_iteration")
         if per_iter is not None:
             traffic = per_iter * iters / max(n_l, 1)
+    executed = (6.0 / 8.0 if variant == 1 else 1.0) * achieved
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-            "traffic_note": "ncu dram bytes per CGNE iteration (profiles/k_cgne_fp64_256.md) x "
+            "achieved_note": "algorithmic flops of the stencil products (8 per complex "
+                             "multiply-add, the operation's definition) per launch / average "
+                             "launch time; the three-FMA form executes 6 of them",
+            "executed_TFLOPs": executed, "executed_frac": executed / FP64_PEAK_TFLOPS,
+            "traffic_note": "ncu dram bytes per CGNE iteration (profiles/k_cgne64_fp64_256.md) x "
                             "iterations per launch; null if the kernel changed since",
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 FMA probe: 1.196 "
                            "TFLOP/s at 1995 MHz)",
@@ -858,8 +878,11 @@ def main():
         g = sw.sw_gauge_load(ctx, th)
         pm = presets.make_params(sw, presets.FP64_256)
         pm.precision = sw.SW_MG_MIXED
+        if args.batch_f32:
+            pm.batch_iterates = sw.SW_PREC_FP32
         hm = sw.sw_mg_setup(g, WORKLOAD["mass"], 3, WORKLOAD["blocks"], WORKLOAD["nvec"],
                             params=pm, psi0=psi0)
+        hm.batch_iterates = 1 if args.batch_f32 else 0
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         xref = {0: torch.zeros(args.L * args.L, dtype=torch.complex128, device="cuda")}
         sw.sw_mg_solve(hm, torch.from_numpy(rhs(rhs_seed(rank, 0, 500), args.L)).cuda(),

@@ -115,6 +115,7 @@ class Server:
     """Multi-worker solve server on one GPU.
 
     gauges: list of (theta [2, L, L], label).  masses: the mass grid.
+    psi0_fn: optional function (L, blocks, nvec) -> initial null-vector guesses.
     workers: number of concurrent streams.  hbm_budget: bytes that resident
     hierarchies may use in total.  sm_share: (num, den) share of the SMs each
     worker's persistent coarsest kernels hold (default 1/workers, so that the
@@ -124,11 +125,13 @@ class Server:
     round-robin in order of first use), which serves all of its requests, so
     each hierarchy is set up once and its queued requests meet in one queue
     for batching; without it any free worker takes any request and builds the
-    hierarchies it needs itself."""
+    hierarchies it needs itself.  hier_cfg: optional function L -> (blocks,
+    nvec) giving the hierarchy of a lattice size (default: blocks and nvec for
+    every size), e.g. one more level for the largest lattices."""
 
     def __init__(self, gauges, masses, workers=2, hbm_budget=40 << 30, tol=1e-10, mixed=True,
                  blocks=((4, 4), (2, 2)), nvec=(24, 32), params=None, device=0, psi0_fn=None,
-                 batch_max=1, sm_share=None, affinity=False):
+                 batch_max=1, sm_share=None, affinity=False, hier_cfg=None):
         import torch
         if int(batch_max) > 1 and not mixed:
             raise ValueError("batch_max > 1 needs mixed=True: sw_mg_solve_batch batches the "
@@ -140,6 +143,7 @@ class Server:
         self.mixed = mixed
         self.blocks = [tuple(b) for b in blocks]
         self.nvec = list(nvec)
+        self.hier_cfg = hier_cfg
         self.params = params or {}
         self.budget = hbm_budget
         self.psi0_fn = psi0_fn
@@ -220,11 +224,18 @@ class Server:
             wk["ctx"].free()
 
     # ------------------------------------------------------------------ workers
+    def _cfg(self, L: int):
+        if self.hier_cfg is None:
+            return self.blocks, self.nvec
+        blocks, nvec = self.hier_cfg(L)
+        return [tuple(b) for b in blocks], list(nvec)
+
     def _footprint(self, gauge: int) -> int:
         L = self.gauges[gauge][0].shape[-1]
-        b = hierarchy_bytes(L, self.blocks, self.nvec, self.mixed)
+        blocks, nvec = self._cfg(L)
+        b = hierarchy_bytes(L, blocks, nvec, self.mixed)
         if self.batch_max > 1 and self.mixed:
-            b += batch_workspace_bytes(L, self.blocks, self.nvec)
+            b += batch_workspace_bytes(L, blocks, nvec, width=min(64, 2 * self.batch_max))
         return b
 
     def _companions(self, r):
@@ -271,10 +282,11 @@ class Server:
         if self.mixed:
             p.precision = SW_MG_MIXED
         L = self.gauges[gauge][0].shape[-1]
-        psi0 = self.psi0_fn(L) if self.psi0_fn else None
+        blocks, nvec = self._cfg(L)
+        psi0 = self.psi0_fn(L, blocks, nvec) if self.psi0_fn else None
         with self.torch.cuda.stream(wk["stream"]):
-            mg = sw_mg_setup(wk["gauges"][gauge], mass, len(self.nvec) + 1, self.blocks,
-                             self.nvec, params=p, psi0=psi0)
+            mg = sw_mg_setup(wk["gauges"][gauge], mass, len(nvec) + 1, blocks, nvec, params=p,
+                             psi0=psi0)
         wk["cache"][key] = dict(mg=mg, bytes=need, last=time.perf_counter())
         return wk["cache"][key]
 

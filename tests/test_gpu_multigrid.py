@@ -659,3 +659,29 @@ def test_config3_mixed_512(sw, ctx):
     hmx.free()
     h64.free()
     g.free()
+
+
+def test_coarsest_cap_256_stagnates_at_nv_24_32(sw, ctx):
+    """Record of the coarsest-cap reading of the 256^2 workload (beta 6, 2000
+    sweeps, m = 1e-3, Nv 24/32): with Table kcycle's coarsest cap of 256 CGNE
+    iterations the intermediate GCR stalls and 40 outer iterations leave the
+    true residual above 1e-3, while the workload's cap of 2048 converges to
+    1e-10 in at most 15 outer iterations (the paper leaves the cap to the
+    implementation, Sec. IV.A)."""
+    from paper_1801_07823_gb300 import presets
+    L, m, blocks, nvec = 256, 1e-3, [(4, 4), (2, 2)], [24, 32]
+    th = si.heatbath_u1(L, L, 6.0, 2000, seed=1, device="cuda")
+    psi0 = si.null_vector_guesses(L, L, nvec, 3, blocks)
+    g = sw.sw_gauge_load(ctx, th)
+    b = si.gaussian_complex(1003, L * L)
+    res = {}
+    for cap, outer in ((256, 40), (2048, 40)):
+        p = presets.make_params(sw, presets.FP64_256)
+        p.coarsest_maxiter, p.outer_maxiter = cap, outer
+        h = sw.sw_mg_setup(g, m, 3, blocks, nvec, params=p, psi0=psi0)
+        x = np.zeros_like(b)
+        res[cap] = sw.sw_mg_solve(h, b, x, 1e-10, allow_noconv=True)
+        h.free()
+    g.free()
+    assert not res[256]["converged"] and res[256]["true_resid"] > 1e-3, res[256]
+    assert res[2048]["converged"] and res[2048]["outer_iters"] <= 15, res[2048]

@@ -29,7 +29,7 @@ def test_serving_results_alone_equal_mixed(batch_max):
         L = gauges[gid][0].shape[-1]
         m = float(np.exp(rng.uniform(np.log(1e-2), np.log(1e-1))))
         reqs.append((gid, m, si.gaussian_complex(500 + i, L * L)))
-    psi0 = lambda L: psi0_arrays(L, L, [8, 12], 3, [(4, 4), (2, 2)])
+    psi0 = lambda L, blocks, nvec: psi0_arrays(L, L, nvec, len(nvec) + 1, blocks)
     kw = dict(nvec=(8, 12), psi0_fn=psi0, hbm_budget=8 << 30, params=dict(outer_maxiter=300),
               batch_max=batch_max, sm_share=(1, 3))
     alone = serve.Server(gauges, masses, workers=1, **kw)

@@ -175,7 +175,8 @@ def test_requests_on_one_hierarchy_are_batched(fake):
         s = serve.latency_summary(srv.done)
         assert s["mean_batch"] > 1.0
         one = serve.hierarchy_bytes(16, [(4, 4), (2, 2)], [24, 32], True)
-        assert srv._footprint(0) == one + serve.batch_workspace_bytes(16, [(4, 4), (2, 2)], [24, 32])
+        assert srv._footprint(0) == one + serve.batch_workspace_bytes(16, [(4, 4), (2, 2)], [24, 32],
+                                                                      width=8)
     finally:
         srv.close()
 
