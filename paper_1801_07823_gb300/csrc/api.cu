@@ -19,6 +19,14 @@ void report_stale_error(cudaError_t e) {
                  cudaGetErrorString(e));
 }
 
+void sw_poison(void* p, size_t bytes) {
+  static const bool on = [] {
+    const char* e = std::getenv("SW_POISON");
+    return e && e[0] == '1';
+  }();
+  if (on && p && bytes) SW_CUDA(cudaMemset(p, 0xFF, bytes));  // all-ones: a NaN in every double
+}
+
 void dev_free(void* p, const char* what) {
   if (!p) return;
   cudaError_t e = cudaFree(p);
@@ -59,6 +67,7 @@ T* dmalloc(size_t count) {
     cudaGetLastError();
     throw SwError{SW_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)};
   }
+  sw_poison(p, count * sizeof(T));
   return (T*)p;
 }
 

@@ -155,14 +155,14 @@ __global__ void k_restrict_fine(const double2* __restrict__ P, const double2* __
   int c = t / nv, i = t - c * nv;
   int ka = c ? 1 : 0, kb = c ? 2 : 3;
   double2 acc = make_double2(0.0, 0.0);
-  int half = (L0 * L1) >> 1;
+  const int N = L0 * L1;
   for (int by = 0; by < a1; ++by)
     for (int bx = 0; bx < a0; ++bx) {
       int X0 = A0 * a0 + bx, X1 = A1 * a1 + by;
-      int par = (X0 + X1) & 1;
-      if (par && !full) continue;
-      int hb = par * half + X1 * (L0 >> 2) + (X0 >> 1);
-      int ha = 4 * hb + ka, hc = 4 * hb + kb;
+      if (((X0 + X1) & 1) && !full) continue;
+      // the two sites k = ka, kb of KD block (X0, X1), parity-split positions
+      int ha = ps_index(2 * X0 + (ka & 1), 2 * X1 + (ka >> 1), L0, N);
+      int hc = ps_index(2 * X0 + (kb & 1), 2 * X1 + (kb >> 1), L0, N);
       cfmac(acc, P[(long)ha * nv + i], r_e[ha]);
       cfmac(acc, P[(long)hc * nv + i], r_e[hc]);
     }

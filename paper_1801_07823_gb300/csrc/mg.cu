@@ -41,6 +41,7 @@ double2* dalloc(long n) {
     throw SwError{SW_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(n * 16) +
                                   " bytes failed: " + cudaGetErrorString(e)};
   }
+  sw_poison(p, n * sizeof(double2));
   return (double2*)p;
 }
 
@@ -128,6 +129,15 @@ static void check_norm(double v, const char* where) {
   if (!std::isfinite(v)) throw SwError{SW_ERR_NAN, std::string("non-finite norm in ") + where};
 }
 
+// SW_VERBOSE >= 3: the 2-norm of a work vector on stderr (a trace of where a
+// non-finite value first appears).  Costs a host round trip per call.
+static void trace_norm(sw_mg* mg, int l, const char* what, const double2* v, long n) {
+  if (mg->verbose < 3) return;
+  blas_norm2(mg->ctx, v, n, slot_base(l) + 63);
+  std::fprintf(stderr, "[sw]       level %d %s |v| %.6e\n", l + 1, what,
+               std::sqrt(slot_read(mg->ctx, slot_base(l) + 63).x));
+}
+
 // ---------------------------------------------------------------- Krylov
 // MR smoother with zero initial guess: x, r = b - op x.
 static void mr(sw_mg* mg, int l, const double2* b, double2* x, double2* r, double2* q) {
@@ -142,6 +152,11 @@ static void mr(sw_mg* mg, int l, const double2* b, double2* x, double2* r, doubl
     level_op(mg, l, r, q, nullptr, lowp);
     blas_dot(c, q, r, n, sq);
     blas_norm2(c, q, n, sqq);
+    if (mg->verbose >= 3) {
+      const double2 a = slot_read(c, sq), b = slot_read(c, sqq);
+      std::fprintf(stderr, "[sw]       level %d MR %d (q, r) %.6e %+.6ei |q|^2 %.6e\n", l + 1,
+                   it, a.x, a.y, b.x);
+    }
     blas_axpy(c, x, r, n, coef_ratio(sq, sqq, om));
     blas_axpy(c, r, q, n, coef_ratio(sq, sqq, -om));
   }
@@ -156,11 +171,15 @@ static void kcycle(sw_mg* mg, int l, const double2* r, double2* out) {
   MgLevel& C = mg->lev[l + 1];
   long n = level_len(mg, l);
   cudaStream_t s = c->stream;
+  trace_norm(mg, l, "K-cycle input", r, n);
   mr(mg, l, r, L.kx1, L.kr1, L.kq);
+  trace_norm(mg, l, "pre-smoothed x", L.kx1, n);
+  trace_norm(mg, l, "pre-smoothed r", L.kr1, n);
   if (l == 0)
     launch_restrict_fine(mg->g, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s, mg->fine_D ? 1 : 0);
   else
     launch_restrict_coarse(CoarseGeom{L.E0, L.E1, L.nc}, L.b0, L.b1, L.nv, L.P, L.kr1, C.rhs, s);
+  trace_norm(mg, l + 1, "restricted r", C.rhs, level_len(mg, l + 1));
   solve_level(mg, l + 1, C.rhs, C.sol);
   if (l == 0)
     launch_prolong_fine(mg->g, L.b0, L.b1, L.nv, L.P, C.sol, L.ke, s, mg->fine_D ? 1 : 0);
@@ -384,6 +403,8 @@ static int cgne(sw_mg* mg, int l, const double2* b, double2* x) {
       if (c->h_ctl[1])
         throw SwError{SW_ERR_TIMEOUT, "coarsest CGNE: a grid barrier wait gave up"};
       if (c->h_ctl[2]) throw SwError{SW_ERR_NAN, "non-finite norm in CGNE residual"};
+      if (mg->verbose > 1)
+        std::fprintf(stderr, "[sw]     coarsest CGNE launch: %d iterations\n", c->h_ctl[0]);
       return c->h_ctl[0];
     }
   }

@@ -29,6 +29,10 @@ void sw_count_launch();
     sw_count_launch();            \
     SW_CUDA(cudaGetLastError());  \
   } while (0)
+// Debug aid: with the environment variable SW_POISON=1 every device buffer the
+// library allocates is filled with all-one bytes (NaN in every double and
+// float), so that a kernel reading memory nothing has written produces NaN.
+void sw_poison(void* p, size_t bytes);
 // cudaFree that reports a failure on stderr (and clears it) instead of
 // leaving it pending for the next launch check.
 void dev_free(void* p, const char* what);

@@ -396,6 +396,20 @@ def test_galerkin_mg_of_D_negative_control(sw, ctx):
     e0, e1, nc = sw.sw_mg_level_info(h, 2)
     Ag = assemble_stencil(sw.sw_mg_export_Y(h, 2), e0, e1)
     assert relerr(Ag, H.levels[1].op.toarray()) < 1e-10
+    # level-1 transfers act on every site (both KD-block parities): R = P^dag
+    # and P of the oracle's D-variant prolongator
+    lev = H.levels[0]
+    Pg = sw.sw_mg_export_P(h, 1, nvec[0])
+    Pref = compact_P(lev.P, lev.chir, lattice.fine_aggregate(L, L, *blocks[0]), nvec[0])
+    assert relerr(Pg, Pref) < 1e-10
+    v = si.gaussian_complex(50, L * L)
+    out = np.zeros(e0 * e1 * nc, dtype=complex)
+    sw.sw_mg_transfer(h, 1, 0, v, out)
+    assert relerr(out, lev.P.conj().T @ v) < 1e-10
+    eh = si.gaussian_complex(51, out.size)
+    back = np.zeros(L * L, dtype=complex)
+    sw.sw_mg_transfer(h, 1, 1, eh, back)
+    assert relerr(back, lev.P @ eh) < 1e-10
     h.free()
     b = si.gaussian_complex(1003, L * L)
     res = {}
