@@ -40,6 +40,7 @@
 // and MMAs it has in flight, frees its tensor memory and leaves at the next
 // grid barrier, where every other CTA sees the status and leaves too.
 #pragma once
+#include <cstring>
 #include <string>
 
 #include "sw_internal.h"
@@ -91,6 +92,25 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       "l"(src), "r"(bytes), "r"(su32(b))
       : "memory");
 }
+// The same bulk copy with an L2 eviction-priority policy (createpolicy).
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, unsigned bytes,
+                                               unsigned long long* b, unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(b)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ void fence_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -106,10 +126,26 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void epi_sync() {  // named barrier of the epilogue warps
   asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
 }
-__device__ __forceinline__ float to_tf32(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// Rounds an FP32 value to TF32 (10 explicit mantissa bits), to nearest with
+// ties away from zero, by integer arithmetic on its bits: add half a unit of
+// the last kept place to the magnitude bits and clear the 13 dropped bits (a
+// carry into the exponent is the correct rounding up).  The tensor cores then
+// read exactly this value.
+__host__ __device__ __forceinline__ float to_tf32(float x) {
+#ifdef __CUDA_ARCH__
+  unsigned u = __float_as_uint(x);
+#else
+  unsigned u;
+  std::memcpy(&u, &x, 4);
+#endif
+  u = (u + 0x1000u) & 0xFFFFE000u;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float y;
+  std::memcpy(&y, &u, 4);
+  return y;
+#endif
 }
 
 // Shared-memory matrix descriptor, K-major without swizzle: start address,
@@ -321,6 +357,7 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
   if (t == 0) {
     // ---------------- producer: one (site, direction) pair per stage
     fence_async_global();
+    const unsigned long long pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
     for (int it = 0; it < nitems && !aborted(sm); ++it) {
       const unsigned q = pp.q + it;
       const int s = q % S;
@@ -334,8 +371,12 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
       const int nb = nbr(X, d, a.E0, a.E1);
       unsigned char* buf = stages + (size_t)s * C::kStage;
       mbar_expect(&sm.full[s], (unsigned)C::kStage);
-      bulk_load(buf, Ablk + ((size_t)X * 5 + d) * (C::kATile / 4), C::kATile, &sm.full[s]);
-      bulk_load(buf + C::kATile, Vt + (size_t)nb * (C::kBTile / 4), C::kBTile, &sm.full[s]);
+      // stencil tiles are read once per phase: evict first; right-hand-side
+      // tiles are read by the five sites around their own: keep them
+      bulk_load_hint(buf, Ablk + ((size_t)X * 5 + d) * (C::kATile / 4), C::kATile, &sm.full[s],
+                     pol_stream);
+      bulk_load_hint(buf + C::kATile, Vt + (size_t)nb * (C::kBTile / 4), C::kBTile, &sm.full[s],
+                     pol_keep);
       sm.issued = q + 1;
     }
   } else if (t == 32) {
