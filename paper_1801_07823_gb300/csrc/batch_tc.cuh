@@ -42,6 +42,7 @@
 #pragma once
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "sw_internal.h"
 
@@ -416,9 +417,40 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
     // ---------------- epilogue: one TMEM lane (stacked row) per thread
     const int e = t - 128;                 // 0 .. 127
     const int lrow = e;                    // TMEM lane = row of the stacked product
+    constexpr int kg = K < 16 ? K : 16;    // right-hand sides per group
+    constexpr int ngroups = K < 16 ? 1 : K / 16;
+    constexpr int ioff = K < 16 ? K : 16;  // exchange column of the first imaginary-part product
+    // this thread's work item in every group: right-hand side c0 + cr, rows
+    // grp * 8 .. grp * 8 + 7 of the site
+    const bool has_item = e < kg * C::kGroups;
+    const int cr = e % kg, grp = e / kg;
+    using V = typename std::conditional<F32, float2, double2>::type;
+    V* Xv = reinterpret_cast<V*>(a.X);
+    V* Rv = reinterpret_cast<V*>(a.R);
+    V* Pv = reinterpret_cast<V*>(a.P);
+    V xv[8], rv[8], pv[8];
+    // The iterates of a group do not depend on the products, so their loads
+    // are issued before the group's tensor-memory read (group 0's before the
+    // wait for the site's accumulator tile) and their latency overlaps it.
+    auto load_group = [&](int X, int g) {
+      if (!has_item) return;
+      const size_t el0 = ((size_t)X * NC + grp * 8) * K + (K < 16 ? 0 : 16 * g) + cr;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (MODE == kXR) {
+          xv[k] = __ldcg(Xv + el0 + k * K);
+          rv[k] = __ldcg(Rv + el0 + k * K);
+          pv[k] = __ldcg(Pv + el0 + k * K);
+        } else if (MODE == kP) {
+          pv[k] = __ldcg(Pv + el0 + k * K);
+        }
+      }
+    };
     for (int m = 0; m < nmine; ++m) {
       const unsigned at = pp.a + m;
       const int tile = at & 1;
+      const int X = cta + G * m;
+      load_group(X, 0);
       // one thread waits for the tile; the decision is shared so that every
       // epilogue thread takes the same branch at the named barriers below
       if (e == 0) {
@@ -432,12 +464,12 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
       epi_sync();
       if (!sm.epi_go) break;
       tc_fence_after();
-      const int X = cta + G * m;
       // the combination of group g needs columns [16 g, 16 g + 16) and
       // [K + 16 g, K + 16 g + 16) of rows i and i + NC
-      for (int g = 0; g < K / 16 || (K < 16 && g == 0); ++g) {
+      for (int g = 0; g < ngroups; ++g) {
         const int c0 = K < 16 ? 0 : 16 * g;       // K = 8: both halves in one 16-column load
         const unsigned lane_base = ((unsigned)(32 * (warp - 4))) << 16;
+        if (g > 0) load_group(X, g);
         epi_sync();  // previous group's readers are done with exch
         {
           float w[32];
@@ -446,130 +478,104 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
 #pragma unroll
             for (int c = 0; c < 16; ++c) exch[lrow * 32 + ((c + lrow) & 31)] = w[c];
           } else {
+            // (c0 & 31) and ((K + c0) & 31) are 0 or 16: select between two
+            // static halves so that w stays in registers
+            const bool h0 = (c0 & 31) != 0, h1 = ((K + c0) & 31) != 0;
             tmem_ld32(sm.tmem + lane_base + tile * C::kN + (c0 & ~31), w);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) exch[lrow * 32 + ((c + lrow) & 31)] = w[(c0 & 31) + c];
+            for (int c = 0; c < 16; ++c)
+              exch[lrow * 32 + ((c + lrow) & 31)] = h0 ? w[16 + c] : w[c];
             tmem_ld32(sm.tmem + lane_base + tile * C::kN + ((K + c0) & ~31), w);
 #pragma unroll
             for (int c = 0; c < 16; ++c)
-              exch[lrow * 32 + ((16 + c + lrow) & 31)] = w[((K + c0) & 31) + c];
+              exch[lrow * 32 + ((16 + c + lrow) & 31)] = h1 ? w[16 + c] : w[c];
           }
         }
         epi_sync();
+        if (!has_item) continue;
         // combine: columns 0..15 hold Re-part products of rhs c0 + c (K = 8: 0..7),
         // columns 16..31 those of the imaginary parts (K = 8: columns 8..15)
-        const int kg = K < 16 ? K : 16;
-        const int ioff = K < 16 ? K : 16;  // column of the first imaginary-part product
-        for (int pidx = e; pidx < kg * C::kGroups; pidx += kEpiThreads) {
-          const int cr = pidx % kg, grp = pidx / kg, r = c0 + cr;
-          float* vt = (MODE == kXR ? a.Rt : a.Pt) + (size_t)X * (C::kBTile / 4);
-          const size_t el0 = ((size_t)X * NC + grp * 8) * K + r;  // row grp * 8, step K
-          // the eight rows' products, then all their loads, then the updates
-          float re[8], im[8];
+        const int r = c0 + cr;
+        float* vt = (MODE == kXR ? a.Rt : a.Pt) + (size_t)X * (C::kBTile / 4);
+        const size_t el0 = ((size_t)X * NC + grp * 8) * K + r;  // row grp * 8, step K
+        float re[8], im[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int i = grp * 8 + k;
+          auto E = [&](int row, int col) { return exch[row * 32 + ((col + row) & 31)]; };
+          re[k] = E(i, cr) - E(i + NC, ioff + cr);
+          im[k] = E(i, ioff + cr) + E(i + NC, cr);
+        }
+        const bool live = MODE == kInit || sm.state[r] == 0;
+        double q2 = 0.0;
+        if constexpr (F32) {
+          const float cf = sm.coef_f[r];
+          float s8 = 0.f;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int i = grp * 8 + k;
-            auto E = [&](int row, int col) { return exch[row * 32 + ((col + row) & 31)]; };
-            re[k] = E(i, cr) - E(i + NC, ioff + cr);
-            im[k] = E(i, ioff + cr) + E(i + NC, cr);
-          }
-          const bool live = MODE == kInit || sm.state[r] == 0;
-          double q2 = 0.0;
-          if (F32) {
-            float2* Xf = reinterpret_cast<float2*>(a.X);
-            float2* Rf = reinterpret_cast<float2*>(a.R);
-            float2* Pf = reinterpret_cast<float2*>(a.P);
-            float2 xv[8], rv[8], pv[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              if (MODE == kXR) {
-                xv[k] = __ldcg(Xf + el0 + k * K);
-                rv[k] = __ldcg(Rf + el0 + k * K);
-                pv[k] = __ldcg(Pf + el0 + k * K);
-              } else if (MODE == kP) {
-                pv[k] = __ldcg(Pf + el0 + k * K);
+            float2 o;
+            if (MODE == kXR) {
+              o = rv[k];
+              if (live) {
+                float2 xn = xv[k];
+                xn.x = fmaf(cf, pv[k].x, xn.x);
+                xn.y = fmaf(cf, pv[k].y, xn.y);
+                o.x = fmaf(-cf, re[k], o.x);
+                o.y = fmaf(-cf, im[k], o.y);
+                Xv[el0 + k * K] = xn;
+                Rv[el0 + k * K] = o;
               }
-            }
-            const float cf = sm.coef_f[r];
-            float s8 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int i = grp * 8 + k;
-              float2 o;
-              if (MODE == kXR) {
-                o = rv[k];
+            } else {
+              o = make_float2(re[k], im[k]);
+              if (MODE == kP) {
+                o = pv[k];
                 if (live) {
-                  xv[k].x = fmaf(cf, pv[k].x, xv[k].x);
-                  xv[k].y = fmaf(cf, pv[k].y, xv[k].y);
-                  o.x = fmaf(-cf, re[k], o.x);
-                  o.y = fmaf(-cf, im[k], o.y);
-                  Xf[el0 + k * K] = xv[k];
-                  Rf[el0 + k * K] = o;
+                  o.x = fmaf(cf, o.x, re[k]);
+                  o.y = fmaf(cf, o.y, im[k]);
                 }
-              } else {
-                o = make_float2(re[k], im[k]);
-                if (MODE == kP) {
-                  o = pv[k];
-                  if (live) {
-                    o.x = fmaf(cf, o.x, re[k]);
-                    o.y = fmaf(cf, o.y, im[k]);
-                  }
-                }
-                if (live) Pf[el0 + k * K] = o;
               }
-              if (live) s8 = fmaf(o.x, o.x, fmaf(o.y, o.y, s8));
-              vt[tile_off(r, i, C::kN) / 4] = to_tf32(o.x);
-              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32(o.y);
+              if (live) Pv[el0 + k * K] = o;
             }
-            q2 = (double)s8;
-          } else {
-            double2* Xd = reinterpret_cast<double2*>(a.X);
-            double2* Rd = reinterpret_cast<double2*>(a.R);
-            double2* Pd = reinterpret_cast<double2*>(a.P);
-            double2 xv[8], rv[8], pv[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              if (MODE == kXR) {
-                xv[k] = __ldcg(Xd + el0 + k * K);
-                rv[k] = __ldcg(Rd + el0 + k * K);
-                pv[k] = __ldcg(Pd + el0 + k * K);
-              } else if (MODE == kP) {
-                pv[k] = __ldcg(Pd + el0 + k * K);
-              }
-            }
-            const double cd = sm.coef[r];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int i = grp * 8 + k;
-              double2 o;
-              if (MODE == kXR) {
-                o = rv[k];
-                if (live) {
-                  xv[k].x = fma(cd, pv[k].x, xv[k].x);
-                  xv[k].y = fma(cd, pv[k].y, xv[k].y);
-                  o.x = fma(-cd, (double)re[k], o.x);
-                  o.y = fma(-cd, (double)im[k], o.y);
-                  Xd[el0 + k * K] = xv[k];
-                  Rd[el0 + k * K] = o;
-                }
-              } else {
-                o = make_double2((double)re[k], (double)im[k]);
-                if (MODE == kP) {
-                  o = pv[k];
-                  if (live) {
-                    o.x = fma(cd, o.x, (double)re[k]);
-                    o.y = fma(cd, o.y, (double)im[k]);
-                  }
-                }
-                if (live) Pd[el0 + k * K] = o;
-              }
-              if (live) q2 += fma(o.x, o.x, o.y * o.y);
-              vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)o.x);
-              vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)o.y);
-            }
+            if (live) s8 = fmaf(o.x, o.x, fmaf(o.y, o.y, s8));
+            vt[tile_off(r, i, C::kN) / 4] = to_tf32(o.x);
+            vt[tile_off(K + r, i, C::kN) / 4] = to_tf32(o.y);
           }
-          sm.sq[r * C::kGroups + grp] = q2;
+          q2 = (double)s8;
+        } else {
+          const double cd = sm.coef[r];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int i = grp * 8 + k;
+            double2 o;
+            if (MODE == kXR) {
+              o = rv[k];
+              if (live) {
+                double2 xn = xv[k];
+                xn.x = fma(cd, pv[k].x, xn.x);
+                xn.y = fma(cd, pv[k].y, xn.y);
+                o.x = fma(-cd, (double)re[k], o.x);
+                o.y = fma(-cd, (double)im[k], o.y);
+                Xv[el0 + k * K] = xn;
+                Rv[el0 + k * K] = o;
+              }
+            } else {
+              o = make_double2((double)re[k], (double)im[k]);
+              if (MODE == kP) {
+                o = pv[k];
+                if (live) {
+                  o.x = fma(cd, o.x, (double)re[k]);
+                  o.y = fma(cd, o.y, (double)im[k]);
+                }
+              }
+              if (live) Pv[el0 + k * K] = o;
+            }
+            if (live) q2 += fma(o.x, o.x, o.y * o.y);
+            vt[tile_off(r, i, C::kN) / 4] = to_tf32((float)o.x);
+            vt[tile_off(K + r, i, C::kN) / 4] = to_tf32((float)o.y);
+          }
         }
+        sm.sq[r * C::kGroups + grp] = q2;
       }
       // tile read: hand it back to the MMA issuer
       tc_fence_before();
@@ -578,7 +584,7 @@ __device__ void tc_phase(const TcArgs& a, unsigned char* stages, float* exch,
       // site sums over row groups in order, then the CTA's running sum
       if (e < K) {
         double sv = 0.0;
-        for (int grp = 0; grp < C::kGroups; ++grp) sv += sm.sq[e * C::kGroups + grp];
+        for (int q = 0; q < C::kGroups; ++q) sv += sm.sq[e * C::kGroups + q];
         sm.cta_sum[e] += sv;
       }
     }
