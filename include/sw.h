@@ -199,9 +199,10 @@ int sw_mg_solve(sw_mg* mg, const void* b, void* x, double tol, int on_device,
  * and the coarsest-level solves of all of them run in one batched kernel that
  * reads the coarsest stencil once per batch: its stencil products run on the
  * tensor cores (tcgen05, TF32 operands, FP32 accumulation) for coarse dof
- * counts 16, 24, 32, 48 and 64, with a pipeline depth picked by timing on
- * first use (sw_autotune_entries); iterates and Krylov scalars stay FP64, and
- * so does the outer FGCR.  Larger nrhs run in groups of 64.  A right-hand
+ * counts 16, 24 and 64 (other counts run the same iteration on the CUDA
+ * cores in FP32), with a pipeline depth and an L2 policy picked by timing on
+ * first use (sw_autotune_entries); iterates and Krylov scalars stay FP64
+ * unless params.batch_iterates is SW_PREC_FP32, and the outer FGCR is FP64.  Larger nrhs run in groups of 64.  A right-hand
  * side's scalars do not depend on the others in its batch.
  * Returns SW_ERR_NOCONV if any right-hand side did not converge. */
 int sw_mg_solve_batch(sw_mg* mg, int nrhs, const void* B, void* X, double tol, int on_device,
@@ -326,7 +327,9 @@ int sw_debug_batch_stall(sw_mg* mg, int nrhs);
  * site nc[k], the batch width K[k], the number of coarse sites, the choice and
  * its measured microseconds per CGNE iteration.  For the batched tensor-core
  * coarsest kernel (K = 8, 16, 32 or 64; 100 + K with FP32 iterates) the
- * choice is its pipeline depth; for
+ * choice is its pipeline depth S, or 10 + S when part of its stencil tiles is
+ * loaded with L2 evict-last priority (kept across iterations) instead of
+ * streamed; for
  * the single-right-hand-side FP64 coarsest kernel (K = 1) it is the product
  * form (0: four real FMAs per complex multiply-add, 1: three, with a stored
  * sum plane).  Fills at most max entries (any pointer may be NULL) and returns

@@ -42,6 +42,17 @@ bool tc_supported(int nc) { return nc == 16 || nc == 24 || nc == 64; }
 
 long tc_tile_floats(int nc) { return 128L * nc; }
 
+// Fraction of the stacked stencil tiles (forward and adjoint) that fits in
+// three quarters of the L2 cache, for the evict-last variant.
+float tc_l2_fraction(const CoarseGeom& g, int device) {
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) != cudaSuccess || l2 <= 0)
+    return 0.5f;
+  const double bytes = 2.0 * g.E0 * g.E1 * 5 * tc_tile_floats(g.nc) * 4;
+  const double f = 0.75 * l2 / bytes;
+  return (float)(f > 1.0 ? 1.0 : (f < 0.05 ? 0.05 : f));
+}
+
 void launch_stack_tiles(const CoarseGeom& g, const double2* Y, float* T, int adj, cudaStream_t s) {
   k_stack_tiles<<<g.E0 * g.E1 * 5, 256, 0, s>>>(Y, T, g.E0, g.E1, g.nc, adj);
   SW_LAUNCH_CHECK();
@@ -64,13 +75,13 @@ bool launch_cgne_tc(const CoarseGeom& g, int stages, bool f32, const float* At, 
                     int nb, const double2* const* b, double2* const* x, double2* X, double2* R,
                     double2* P, float* Rt, float* Pt, double* partials, unsigned* bar,
                     int* status, int maxit, double tol, int device, cudaStream_t s, int stall,
-                    int sms_use) {
+                    int sms_use, float l2frac) {
   const int K = tc_width(nb);
   if (nb < 1 || nb > kMaxK || !tc_supported(g.nc)) return false;
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, (2 + kMaxK) * sizeof(int), s));
   TcArgs a{At, Ad, b, x, X, R, P, Rt, Pt, partials, bar, status, nb, g.E0, g.E1, maxit, tol,
-           stall};
+           stall, l2frac < 0.f ? 0.f : (l2frac > 1.f ? 1.f : l2frac)};
   switch (g.nc) {
     case 16: return run_nc16(a, K, stages, f32, device, s, sms_use);
     case 24: return run_nc24(a, K, stages, f32, device, s, sms_use);

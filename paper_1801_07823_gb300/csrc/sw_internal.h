@@ -295,16 +295,19 @@ bool launch_cgne_batch(const CoarseGeom& g, const float2* Yf, const float2* Yd, 
 // [n][K] double2 (float2 with f32: FP32 iterates); partials: 2 K SMs doubles;
 // status: 2 + 64 ints ([0] wait timeout or misaligned buffer, [1] non-finite,
 // [2 + r] iterations).  stages: pipeline depth, one of tc_stage_options(nc, K).
+// l2frac: 0 streams the stencil tiles through L2 (evict first); > 0 loads that
+// fraction of their lines with evict-last priority (tc_l2_fraction sizes it).
 int tc_width(int nb);
 bool tc_supported(int nc);
 long tc_tile_floats(int nc);
+float tc_l2_fraction(const CoarseGeom& g, int device);
 int tc_stage_options(int nc, int K, int* out);
 void launch_stack_tiles(const CoarseGeom& g, const double2* Y, float* T, int adj, cudaStream_t s);
 bool launch_cgne_tc(const CoarseGeom& g, int stages, bool f32, const float* At, const float* Ad,
                     int nb, const double2* const* b, double2* const* x, double2* X, double2* R,
                     double2* P, float* Rt, float* Pt, double* partials, unsigned* bar,
                     int* status, int maxit, double tol, int device, cudaStream_t s, int stall,
-                    int sms_use = 1 << 30);
+                    int sms_use = 1 << 30, float l2frac = 0.f);
 // Yd[X][d] = Y[nb(X, d)][opp(d)]^dag in FP32, every block column-major like Y.
 void launch_adjoint_f32(const CoarseGeom& g, const double2* Y, float2* Yd, cudaStream_t s);
 
