@@ -650,14 +650,16 @@ def run_native(args, rank, world, local):
         e0, e1, nc = shapes[2]
         iters = ktimes[6][0]
         n_l, ms_l = ktimes[5]
-        # product form the FP64 kernel's autotuner chose (0: four FMAs, 1: three)
+        # variant the FP64 kernel's autotuner chose (bit 0: three-FMA products, bit 1:
+        # reduce-scatter row sums)
         ch = [e for e in sw.sw_autotune_entries() if e[1] == 1 and e[0] == nc and e[2] == e0 * e1]
         variant = ch[0][3] if ch else None
         per_apply_flop = 8.0 * 5 * nc * nc * e0 * e1
         flop = per_apply_flop * 2 * iters / max(n_l, 1)      # per launch
-        ybytes = (24.0 if variant == 1 else 16.0) * 5 * nc * nc * e0 * e1
+        ybytes = (24.0 if (variant or 0) & 1 else 16.0) * 5 * nc * nc * e0 * e1
         byt = (ybytes + 16.0 * 2 * nc * e0 * e1) * 2 * iters / max(n_l, 1)
-        kname = (f"k_cgne64<{nc}, {'three' if variant == 1 else 'four'}-FMA products> "
+        kname = (f"k_cgne64<{nc}, {'three' if (variant or 0) & 1 else 'four'}-FMA products"
+                 f"{', reduce-scatter row sums' if (variant or 0) & 2 else ''}> "
                  f"(persistent FP64 coarsest CGNE, {e0}x{e1} sites, {nc}x{nc} complex128 blocks, "
                  f"{iters / max(n_l, 1):.0f} iterations = {2 * iters / max(n_l, 1):.0f} stencil "
                  f"applications per launch)")
@@ -675,7 +677,7 @@ def run_native(args, rank, world, local):
                                      "dram_bytes_per_iteration")
         if per_iter is not None:
             traffic = per_iter * iters / max(n_l, 1)
-    executed = (6.0 / 8.0 if variant == 1 else 1.0) * achieved
+    executed = (6.0 / 8.0 if (variant or 0) & 1 else 1.0) * achieved
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,

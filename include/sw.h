@@ -330,10 +330,12 @@ int sw_debug_batch_stall(sw_mg* mg, int nrhs);
  * choice is its pipeline depth S, or 10 + S when part of its stencil tiles is
  * loaded with L2 evict-last priority (kept across iterations) instead of
  * streamed; for
- * the single-right-hand-side FP64 coarsest kernel (K = 1) it is the product
- * form (0: four real FMAs per complex multiply-add, 1: three, with a stored
- * sum plane).  Fills at most max entries (any pointer may be NULL) and returns
- * the number of entries. */
+ * the single-right-hand-side FP64 coarsest kernel (K = 1) it is the variant:
+ * bit 0 the product form (0: four real FMAs per complex multiply-add, 1:
+ * three, with a stored sum plane), bit 1 the row-sum form (0: every lane of a
+ * row sums all partial sums, 1: reduce-scatter of the real and imaginary parts
+ * and a per-component update).  Fills at most max entries (any pointer may be
+ * NULL) and returns the number of entries. */
 int sw_autotune_entries(int max, int* nc, int* K, int* sites, int* stages, double* us);
 
 /* SplitMix64 stream seed used when psi0 is NULL (level = index into psi0,

@@ -35,10 +35,13 @@
 // CTAs in CTA order, so every CTA takes the same decision and every run gives
 // the same bits.
 //
-// Two variants, chosen per hierarchy by timing (mg.cu): the three-FMA product
-// above, whose stencil plus its sum plane takes 1.5 times the bytes of the
-// stencil (at 16^2 x 64 dof: 120 MB, more than the L2 holds), and the plain
-// four-FMA product on the stencil alone (80 MB).  Stencil loads carry an L2
+// Four variants, chosen per hierarchy by timing (mg.cu).  Bit 0 of the
+// variant selects the three-FMA product above, whose stencil plus its sum
+// plane takes 1.5 times the bytes of the stencil (at 16^2 x 64 dof: 126 MB,
+// more than the L2 holds), over the plain four-FMA product on the stencil
+// alone (84 MB).  Bit 1 selects the reduce-scatter row sums and the
+// per-component update (phase_rs), which spend fewer FP64 instructions
+// outside the stencil products.  Stencil loads carry an L2
 // eviction-priority policy: the fraction l2frac of the lines, sized on the host
 // to what the L2 can keep, are marked evict-last and the rest evict-first, so
 // that a cyclic sweep over a stencil larger than the L2 keeps hitting on most
@@ -243,6 +246,82 @@ __device__ __forceinline__ double bfly8(double v) {
 
 enum { kInit = 0, kP1 = 1, kP2 = 2 };
 
+// Component c (0: real, 1: imaginary) of complex element e.
+__device__ __forceinline__ double ld_comp(const double2* v, long e, int c) {
+  return __ldcg(reinterpret_cast<const double*>(v + e) + c);
+}
+__device__ __forceinline__ void st_comp(double2* v, long e, int c, double x) {
+  reinterpret_cast<double*>(v + e)[c] = x;
+}
+
+// Reduce-scatter form of the row sum and update (variants 2 and 3).  Each lane
+// first combines its partial sums into its share of Re and Im (three-FMA form:
+// Re = K1 -+ K2, Im = K1 +- K3); one exchange across lanes q and q ^ 4 leaves
+// lanes 0-3 with Re and lanes 4-7 with Im, and two more levels complete the
+// sums: five FP64 additions per lane instead of nine.  Lanes 0 and 4 then
+// update one component each of the element (x, r and p are read and written
+// per component), which halves the FP64 instructions of the update; the
+// (c, d, c + d, c - d) form is completed with one more exchange.
+template <int NC, bool M3, int MODE>
+__device__ double phase_rs(const Args& a, double coef, unsigned long long pol) {
+  constexpr int kUnitsPerSite = NC / kRows;
+  const int G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = warp & 3, wj = warp >> 2;
+  const int rr = lane >> 3, q = lane & 7;
+  const int comp = (q >> 2) & 1;  // 0: this lane ends with Re, 1: with Im
+  const bool writer = (q & 3) == 0;
+  const int nunits = a.E0 * a.E1 * kUnitsPerSite;
+  const V4* v = MODE == kP1 ? a.p4 : a.r4;
+  double acc = 0.0;
+  for (int u = sub * G + blockIdx.x + 4 * G * wj; u < nunits; u += 16 * G) {  // warp-uniform
+    const int X = u / kUnitsPerSite;
+    const int i = (u - X * kUnitsPerSite) * kRows + rr;
+    double K1, K2, K3;
+    row_part<NC, MODE != kP1, M3>(a, v, X, i, q, pol, K1, K2, K3);
+    double re, im;
+    if (!M3) {
+      re = K1;
+      im = K2;
+    } else if (MODE == kP1) {  // A v
+      re = K1 - K2;
+      im = K1 + K3;
+    } else {  // A^dag v
+      re = K1 + K2;
+      im = K1 - K3;
+    }
+    double w = comp ? im : re;
+    w += __shfl_xor_sync(0xffffffffu, comp ? re : im, 4);
+    w += __shfl_xor_sync(0xffffffffu, w, 2);
+    w += __shfl_xor_sync(0xffffffffu, w, 1);
+    const long e = (long)X * NC + i;
+    double out;  // this lane's component of the new r (P1) or p
+    if (MODE == kP1) {
+      const double pc = ld_comp(a.p, e, comp);
+      const double xc = fma(coef, pc, ld_comp(a.x, e, comp));
+      out = fma(-coef, w, ld_comp(a.r, e, comp));
+      if (writer) {
+        st_comp(a.x, e, comp, xc);
+        st_comp(a.r, e, comp, out);
+      }
+    } else {
+      out = MODE == kP2 ? fma(coef, ld_comp(a.p, e, comp), w) : w;
+      if (writer) st_comp(a.p, e, comp, out);
+    }
+    // (c, d, c + d, c - d): the Re lane adds the Im lane's value, the Im lane
+    // subtracts it from the Re lane's
+    const double other = __shfl_xor_sync(0xffffffffu, out, 4);
+    V4* f = (MODE == kP1 ? a.r4 : a.p4) + e;
+    if (writer) {
+      double* fd = reinterpret_cast<double*>(f);
+      fd[comp] = out;                                // c or d
+      fd[2 + comp] = comp ? other - out : out + other;  // c + d or c - d
+    }
+    if (writer) acc = fma(out, out, acc);
+  }
+  return acc;
+}
+
 // One stencil application over this warp's units fused with its update;
 // returns this thread's share of the new squared norm.
 template <int NC, bool M3, int MODE>
@@ -294,7 +373,15 @@ __device__ double phase(const Args& a, double coef, unsigned long long pol) {
   return acc;
 }
 
-template <int NC, bool M3>
+template <int NC, bool M3, bool RS, int MODE>
+__device__ __forceinline__ double run_phase(const Args& a, double coef, unsigned long long pol) {
+  if constexpr (RS)
+    return phase_rs<NC, M3, MODE>(a, coef, pol);
+  else
+    return phase<NC, M3, MODE>(a, coef, pol);
+}
+
+template <int NC, bool M3, bool RS>
 __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
   __shared__ double red[kWarps];
   __shared__ double bcast;
@@ -337,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     return;
   }
   // p = A^dag r, ||p||^2
-  acc = phase<NC, M3, kInit>(a, 0.0, pol);
+  acc = run_phase<NC, M3, RS, kInit>(a, 0.0, pol);
   cta_partial(acc, red, a.partials + ph * gridDim.x);
   if (!grid_barrier(a.bar, a.status, ++gen)) return;
   {
@@ -348,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
   ph ^= 1;
   int k = 0;
   for (;;) {
-    acc = phase<NC, M3, kP1>(a, sh_coef, pol);  // w = A p; x += alpha p; r -= alpha w
+    acc = run_phase<NC, M3, RS, kP1>(a, sh_coef, pol);  // w = A p; x += alpha p; r -= alpha w
     cta_partial(acc, red, a.partials + ph * gridDim.x);
     if (!grid_barrier(a.bar, a.status, ++gen)) return;
     ++k;
@@ -366,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     }
     ph ^= 1;
     if (sh_state) break;
-    acc = phase<NC, M3, kP2>(a, sh_coef, pol);  // p = A^dag r + beta p
+    acc = run_phase<NC, M3, RS, kP2>(a, sh_coef, pol);  // p = A^dag r + beta p
     cta_partial(acc, red, a.partials + ph * gridDim.x);
     if (!grid_barrier(a.bar, a.status, ++gen)) return;
     {
@@ -390,13 +477,14 @@ __global__ void k_sum_planes(const double2* __restrict__ Y, double* __restrict__
   }
 }
 
-template <int NC, bool M3>
+template <int NC, bool M3, bool RS>
 bool launch_t(const Args& args, int device, cudaStream_t s, int sms_use) {
   static int cached_sms[64] = {0};
   int& sms = cached_sms[device & 63];
   if (sms == 0) {
     int occ = 0, coop = 0, n = 0;
-    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne64<NC, M3>, kThreads, 0));
+    SW_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne64<NC, M3, RS>, kThreads, 0));
     SW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device));
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     if (!coop || occ < 1 || n > kReduceBlocks) return false;
@@ -406,16 +494,21 @@ bool launch_t(const Args& args, int device, cudaStream_t s, int sms_use) {
   const int grid = sms_use < sms ? (sms_use > 0 ? sms_use : 1) : sms;
   Args a = args;
   void* params[] = {&a};
-  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne64<NC, M3>, dim3(grid),
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne64<NC, M3, RS>, dim3(grid),
                                       dim3(kThreads), params, 0, s));
   sw_count_launch();
   return true;
 }
 
+// variant bit 0: three-FMA products; bit 1: reduce-scatter row sums and update
 template <int NC>
 bool launch_v(const Args& a, int variant, int device, cudaStream_t s, int sms_use) {
-  return variant == 1 ? launch_t<NC, true>(a, device, s, sms_use)
-                      : launch_t<NC, false>(a, device, s, sms_use);
+  switch (variant & 3) {
+    case 0: return launch_t<NC, false, false>(a, device, s, sms_use);
+    case 1: return launch_t<NC, true, false>(a, device, s, sms_use);
+    case 2: return launch_t<NC, false, true>(a, device, s, sms_use);
+    default: return launch_t<NC, true, true>(a, device, s, sms_use);
+  }
 }
 
 }  // namespace
@@ -445,11 +538,12 @@ bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const dou
                    int device, cudaStream_t s, int stall_test, int sms_use) {
   if (!cgne64_supported(g.nc)) return false;
   SW_REQUIRE(((size_t)v4 & 31) == 0, SW_ERR_ARG, "CGNE vector forms need 32-byte alignment");
-  SW_REQUIRE(variant == 0 || Ys, SW_ERR_ARG, "three-FMA CGNE needs the sum plane");
+  SW_REQUIRE(variant >= 0 && variant <= 3, SW_ERR_ARG, "FP64 coarsest CGNE variant is 0..3");
+  SW_REQUIRE(!(variant & 1) || Ys, SW_ERR_ARG, "three-FMA CGNE needs the sum plane");
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));
   const long n = (long)g.E0 * g.E1 * g.nc;
-  const long ybytes = (long)g.E0 * g.E1 * 5 * g.nc * g.nc * (variant == 1 ? 24 : 16);
+  const long ybytes = (long)g.E0 * g.E1 * 5 * g.nc * g.nc * ((variant & 1) ? 24 : 16);
   Args a{Y, Ys, b, x, r, p, reinterpret_cast<V4*>(v4), reinterpret_cast<V4*>(v4) + n, partials,
          bar, status, g.E0, g.E1, maxit, tol, stall_test, cgne64_l2_fraction(ybytes, device)};
   switch (g.nc) {

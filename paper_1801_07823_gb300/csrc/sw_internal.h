@@ -266,7 +266,9 @@ bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const 
 
 // FP64 coarsest CGNE in one persistent kernel (cgne64.cu).  variant 1: three
 // real FMAs per complex product, reading Ys = Re + Im of every entry of Y
-// (launch_sum_planes); variant 0: four FMAs on Y alone (Ys may be NULL).
+// (launch_sum_planes); variant 0: four FMAs on Y alone (Ys may be NULL);
+// variants 2 and 3: 0 and 1 with reduce-scatter row sums and a per-component
+// update.
 // v4: 8 n doubles of 32-byte aligned scratch (forms of r and p).  False when
 // nc has no compiled variant.
 bool cgne64_supported(int nc);
