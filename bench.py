@@ -651,7 +651,7 @@ def run_native(args, rank, world, local):
         iters = ktimes[6][0]
         n_l, ms_l = ktimes[5]
         # variant the FP64 kernel's autotuner chose (bit 0: three-FMA products, bit 1:
-        # reduce-scatter row sums)
+        # reduce-scatter row sums, bit 2: operands staged in shared memory)
         ch = [e for e in sw.sw_autotune_entries() if e[1] == 1 and e[0] == nc and e[2] == e0 * e1]
         variant = ch[0][3] if ch else None
         per_apply_flop = 8.0 * 5 * nc * nc * e0 * e1
@@ -659,7 +659,8 @@ def run_native(args, rank, world, local):
         ybytes = (24.0 if (variant or 0) & 1 else 16.0) * 5 * nc * nc * e0 * e1
         byt = (ybytes + 16.0 * 2 * nc * e0 * e1) * 2 * iters / max(n_l, 1)
         kname = (f"k_cgne64<{nc}, {'three' if (variant or 0) & 1 else 'four'}-FMA products"
-                 f"{', reduce-scatter row sums' if (variant or 0) & 2 else ''}> "
+                 f"{', reduce-scatter row sums' if (variant or 0) & 2 else ''}"
+                 f"{', operands staged in shared memory' if (variant or 0) & 4 else ''}> "
                  f"(persistent FP64 coarsest CGNE, {e0}x{e1} sites, {nc}x{nc} complex128 blocks, "
                  f"{iters / max(n_l, 1):.0f} iterations = {2 * iters / max(n_l, 1):.0f} stencil "
                  f"applications per launch)")

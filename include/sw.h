@@ -334,8 +334,10 @@ int sw_debug_batch_stall(sw_mg* mg, int nrhs);
  * bit 0 the product form (0: four real FMAs per complex multiply-add, 1:
  * three, with a stored sum plane), bit 1 the row-sum form (0: every lane of a
  * row sums all partial sums, 1: reduce-scatter of the real and imaginary parts
- * and a per-component update).  Fills at most max entries (any pointer may be
- * NULL) and returns the number of entries. */
+ * and a per-component update), and 7 for variant 3 with its stencil, sum plane
+ * and vector operands staged in shared memory by asynchronous copies.  Fills
+ * at most max entries (any pointer may be NULL) and returns the number of
+ * entries. */
 int sw_autotune_entries(int max, int* nc, int* K, int* sites, int* stages, double* us);
 
 /* SplitMix64 stream seed used when psi0 is NULL (level = index into psi0,

@@ -322,6 +322,157 @@ __device__ double phase_rs(const Args& a, double coef, unsigned long long pol) {
   return acc;
 }
 
+// ---- staged variant (7): the stencil rows, their sum plane and the
+// neighbour's vector forms reach shared memory by asynchronous copies
+// (cp.async), two chunks ahead of the FMAs, so that the loads in flight do not
+// take registers.  A chunk is four t-steps of one direction of one unit; each
+// warp owns three stage buffers of kStageBytes.
+constexpr int kCh = 4;  // t-steps per chunk
+constexpr int kStageBytes = kCh * 32 * 16 + kCh * 32 * 8 + kCh * 8 * 32;  // Y, Ys, vector forms
+constexpr int kStages = 3;
+constexpr int kStagedSmem = kWarps * kStages * kStageBytes;  // 192 KB
+
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp16h(void* dst, const void* src, unsigned long long pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp8h(void* dst, const void* src, unsigned long long pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int NC, int MODE>
+__device__ double phase_st(const Args& a, double coef, unsigned long long pol,
+                           unsigned char* smem) {
+  static_assert(NC % (kQ * kCh) == 0, "a direction must split into whole chunks");
+  constexpr int kUnitsPerSite = NC / kRows;
+  constexpr int kHalves = NC / (kQ * kCh);  // chunks per direction
+  constexpr int kItems = 5 * kHalves;       // chunks per unit
+  constexpr bool DAG = MODE != kP1;
+  const int G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = warp & 3, wj = warp >> 2;
+  const int rr = lane >> 3, q = lane & 7;
+  const int comp = (q >> 2) & 1;
+  const bool writer = (q & 3) == 0;
+  const int nunits = a.E0 * a.E1 * kUnitsPerSite;
+  const int u0 = sub * G + blockIdx.x + 4 * G * wj;  // this warp's units: u0 + m 16 G
+  const int nmine = u0 < nunits ? (nunits - 1 - u0) / (16 * G) + 1 : 0;
+  const int nk = nmine * kItems;
+  const V4* v = MODE == kP1 ? a.p4 : a.r4;
+  unsigned char* mine = smem + (size_t)warp * kStages * kStageBytes;
+  // chunk k into stage k % 3 (an empty group past the end keeps the counting uniform)
+  auto issue = [&](int k) {
+    if (k < nk) {
+      const int m = k / kItems, rem = k - m * kItems, d = rem / kHalves, h = rem - d * kHalves;
+      const int u = u0 + m * 16 * G;
+      const int X = u / kUnitsPerSite;
+      const int i = (u - X * kUnitsPerSite) * kRows + rr;
+      const int nb = nbr(X, d, a.E0, a.E1);
+      const long base = DAG ? ((long)(nb * 5 + opp(d)) * NC + i) * NC + q
+                            : ((long)(X * 5 + d) * NC + q) * NC + i;
+      const long step = DAG ? kQ : (long)kQ * NC;
+      unsigned char* st = mine + (k % kStages) * kStageBytes;
+      double2* Yb = reinterpret_cast<double2*>(st);
+      double* Sb = reinterpret_cast<double*>(st + kCh * 32 * 16);
+      V4* Wb = reinterpret_cast<V4*>(st + kCh * 32 * 24);
+#pragma unroll
+      for (int tt = 0; tt < kCh; ++tt) {
+        const long off = base + (long)(h * kCh + tt) * step;
+        cp16h(Yb + tt * 32 + lane, a.Y + off, pol);
+        cp8h(Sb + tt * 32 + lane, a.Ys + off, pol);
+      }
+      // the chunk's vector forms v[nb NC + (h kCh + tt) 8 + q] are 32
+      // consecutive entries: lane copies entry `lane` (two 16-byte halves)
+      const V4* src = v + (long)nb * NC + h * kCh * kQ + lane;
+      cp16(Wb + lane, src);
+      cp16(reinterpret_cast<unsigned char*>(Wb + lane) + 16,
+           reinterpret_cast<const unsigned char*>(src) + 16);
+    }
+    cp_commit();
+  };
+  double acc = 0.0, K1 = 0.0, K2 = 0.0, K3 = 0.0;
+  issue(0);
+  issue(1);
+  for (int k = 0; k < nk; ++k) {  // warp-uniform
+    __syncwarp();  // every lane is done with chunk k - 1, whose stage chunk k + 2 reuses
+    issue(k + 2);
+    cp_wait<2>();  // this lane's copies of chunk k have landed
+    __syncwarp();  // and so have the other lanes' (vector forms are shared)
+    const unsigned char* st = mine + (k % kStages) * kStageBytes;
+    const double2* Yb = reinterpret_cast<const double2*>(st);
+    const double* Sb = reinterpret_cast<const double*>(st + kCh * 32 * 16);
+    const V4* Wb = reinterpret_cast<const V4*>(st + kCh * 32 * 24);
+#pragma unroll
+    for (int tt = 0; tt < kCh; ++tt) {
+      const double2 y = Yb[tt * 32 + lane];
+      const double sv = Sb[tt * 32 + lane];
+      const V4 w = Wb[tt * kQ + q];
+      if (!DAG) {
+        K1 = fma(sv, w.c, K1);
+        K2 = fma(y.y, w.cpd, K2);
+        K3 = fma(-y.x, w.cmd, K3);
+      } else {
+        K1 = fma(sv, w.d, K1);
+        K2 = fma(y.x, w.cmd, K2);
+        K3 = fma(y.y, w.cpd, K3);
+      }
+    }
+    const int m = k / kItems;
+    if (k - m * kItems != kItems - 1) continue;
+    // unit complete: row sums and update, as in phase_rs
+    const int u = u0 + m * 16 * G;
+    const int X = u / kUnitsPerSite;
+    const int i = (u - X * kUnitsPerSite) * kRows + rr;
+    const double re = DAG ? K1 + K2 : K1 - K2;
+    const double im = DAG ? K1 - K3 : K1 + K3;
+    K1 = K2 = K3 = 0.0;
+    double w = comp ? im : re;
+    w += __shfl_xor_sync(0xffffffffu, comp ? re : im, 4);
+    w += __shfl_xor_sync(0xffffffffu, w, 2);
+    w += __shfl_xor_sync(0xffffffffu, w, 1);
+    const long e = (long)X * NC + i;
+    double out;
+    if (MODE == kP1) {
+      const double pc = ld_comp(a.p, e, comp);
+      const double xc = fma(coef, pc, ld_comp(a.x, e, comp));
+      out = fma(-coef, w, ld_comp(a.r, e, comp));
+      if (writer) {
+        st_comp(a.x, e, comp, xc);
+        st_comp(a.r, e, comp, out);
+      }
+    } else {
+      out = MODE == kP2 ? fma(coef, ld_comp(a.p, e, comp), w) : w;
+      if (writer) st_comp(a.p, e, comp, out);
+    }
+    const double other = __shfl_xor_sync(0xffffffffu, out, 4);
+    V4* f = (MODE == kP1 ? a.r4 : a.p4) + e;
+    if (writer) {
+      double* fd = reinterpret_cast<double*>(f);
+      fd[comp] = out;
+      fd[2 + comp] = comp ? other - out : out + other;
+      acc = fma(out, out, acc);
+    }
+  }
+  cp_wait<0>();
+  return acc;
+}
+
 // One stencil application over this warp's units fused with its update;
 // returns this thread's share of the new squared norm.
 template <int NC, bool M3, int MODE>
@@ -373,16 +524,20 @@ __device__ double phase(const Args& a, double coef, unsigned long long pol) {
   return acc;
 }
 
-template <int NC, bool M3, bool RS, int MODE>
-__device__ __forceinline__ double run_phase(const Args& a, double coef, unsigned long long pol) {
-  if constexpr (RS)
+template <int NC, bool M3, bool RS, bool ST, int MODE>
+__device__ __forceinline__ double run_phase(const Args& a, double coef, unsigned long long pol,
+                                           unsigned char* smem) {
+  if constexpr (ST)
+    return phase_st<NC, MODE>(a, coef, pol, smem);
+  else if constexpr (RS)
     return phase_rs<NC, M3, MODE>(a, coef, pol);
   else
     return phase<NC, M3, MODE>(a, coef, pol);
 }
 
-template <int NC, bool M3, bool RS>
+template <int NC, bool M3, bool RS, bool ST>
 __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
+  extern __shared__ __align__(128) unsigned char stage_smem[];  // staged variant only
   __shared__ double red[kWarps];
   __shared__ double bcast;
   __shared__ double sh_rr, sh_stop, sh_coef;
@@ -424,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     return;
   }
   // p = A^dag r, ||p||^2
-  acc = run_phase<NC, M3, RS, kInit>(a, 0.0, pol);
+  acc = run_phase<NC, M3, RS, ST, kInit>(a, 0.0, pol, stage_smem);
   cta_partial(acc, red, a.partials + ph * gridDim.x);
   if (!grid_barrier(a.bar, a.status, ++gen)) return;
   {
@@ -435,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
   ph ^= 1;
   int k = 0;
   for (;;) {
-    acc = run_phase<NC, M3, RS, kP1>(a, sh_coef, pol);  // w = A p; x += alpha p; r -= alpha w
+    acc = run_phase<NC, M3, RS, ST, kP1>(a, sh_coef, pol, stage_smem);  // w = A p; x += alpha p; r -= alpha w
     cta_partial(acc, red, a.partials + ph * gridDim.x);
     if (!grid_barrier(a.bar, a.status, ++gen)) return;
     ++k;
@@ -453,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     }
     ph ^= 1;
     if (sh_state) break;
-    acc = run_phase<NC, M3, RS, kP2>(a, sh_coef, pol);  // p = A^dag r + beta p
+    acc = run_phase<NC, M3, RS, ST, kP2>(a, sh_coef, pol, stage_smem);  // p = A^dag r + beta p
     cta_partial(acc, red, a.partials + ph * gridDim.x);
     if (!grid_barrier(a.bar, a.status, ++gen)) return;
     {
@@ -477,14 +632,18 @@ __global__ void k_sum_planes(const double2* __restrict__ Y, double* __restrict__
   }
 }
 
-template <int NC, bool M3, bool RS>
+template <int NC, bool M3, bool RS, bool ST>
 bool launch_t(const Args& args, int device, cudaStream_t s, int sms_use) {
   static int cached_sms[64] = {0};
   int& sms = cached_sms[device & 63];
+  const int smem = ST ? kStagedSmem : 0;
   if (sms == 0) {
     int occ = 0, coop = 0, n = 0;
-    SW_CUDA(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne64<NC, M3, RS>, kThreads, 0));
+    if (ST)
+      SW_CUDA(cudaFuncSetAttribute(k_cgne64<NC, M3, RS, ST>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgne64<NC, M3, RS, ST>,
+                                                          kThreads, smem));
     SW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device));
     SW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     if (!coop || occ < 1 || n > kReduceBlocks) return false;
@@ -494,20 +653,25 @@ bool launch_t(const Args& args, int device, cudaStream_t s, int sms_use) {
   const int grid = sms_use < sms ? (sms_use > 0 ? sms_use : 1) : sms;
   Args a = args;
   void* params[] = {&a};
-  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne64<NC, M3, RS>, dim3(grid),
-                                      dim3(kThreads), params, 0, s));
+  SW_CUDA(cudaLaunchCooperativeKernel((const void*)k_cgne64<NC, M3, RS, ST>, dim3(grid),
+                                      dim3(kThreads), params, smem, s));
   sw_count_launch();
   return true;
 }
 
-// variant bit 0: three-FMA products; bit 1: reduce-scatter row sums and update
+// variant bit 0: three-FMA products; bit 1: reduce-scatter row sums and update;
+// 7: both, with the operands staged in shared memory (nc a multiple of 32)
 template <int NC>
 bool launch_v(const Args& a, int variant, int device, cudaStream_t s, int sms_use) {
-  switch (variant & 3) {
-    case 0: return launch_t<NC, false, false>(a, device, s, sms_use);
-    case 1: return launch_t<NC, true, false>(a, device, s, sms_use);
-    case 2: return launch_t<NC, false, true>(a, device, s, sms_use);
-    default: return launch_t<NC, true, true>(a, device, s, sms_use);
+  switch (variant) {
+    case 0: return launch_t<NC, false, false, false>(a, device, s, sms_use);
+    case 1: return launch_t<NC, true, false, false>(a, device, s, sms_use);
+    case 2: return launch_t<NC, false, true, false>(a, device, s, sms_use);
+    case 3: return launch_t<NC, true, true, false>(a, device, s, sms_use);
+    case 7:
+      if constexpr (NC % (kQ * kCh) == 0) return launch_t<NC, true, true, true>(a, device, s, sms_use);
+      return false;
+    default: return false;
   }
 }
 
@@ -521,6 +685,7 @@ void launch_sum_planes(const double2* Y, double* Ys, long n, cudaStream_t s) {
 bool cgne64_supported(int nc) {
   return nc == 16 || nc == 24 || nc == 32 || nc == 48 || nc == 64;
 }
+bool cgne64_staged_supported(int nc) { return nc % (kQ * kCh) == 0 && cgne64_supported(nc); }
 
 // Fraction of a stencil of `bytes` that the L2 can keep resident across a
 // sweep (three quarters of its capacity, the rest left to vectors and other
@@ -538,7 +703,8 @@ bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const dou
                    int device, cudaStream_t s, int stall_test, int sms_use) {
   if (!cgne64_supported(g.nc)) return false;
   SW_REQUIRE(((size_t)v4 & 31) == 0, SW_ERR_ARG, "CGNE vector forms need 32-byte alignment");
-  SW_REQUIRE(variant >= 0 && variant <= 3, SW_ERR_ARG, "FP64 coarsest CGNE variant is 0..3");
+  SW_REQUIRE((variant >= 0 && variant <= 3) || variant == 7, SW_ERR_ARG,
+             "FP64 coarsest CGNE variant is 0..3 or 7");
   SW_REQUIRE(!(variant & 1) || Ys, SW_ERR_ARG, "three-FMA CGNE needs the sum plane");
   SW_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   SW_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));

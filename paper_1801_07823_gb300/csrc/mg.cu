@@ -325,8 +325,11 @@ static std::map<std::tuple<int, int, int, int, int>, TuneRec> g_tune;  // + SMs 
 // data (the real solve then starts from scratch).
 static int cgne64_variant(sw_mg* mg, MgLevel& L, const double2* b, double2* x, int sms) {
   sw_ctx* c = mg->ctx;
-  const char* force = std::getenv("SW_CGNE64");  // "0" .. "3": skip the timing, use this one
-  if (force && force[0] >= '0' && force[0] <= '3' && !force[1]) return force[0] - '0';
+  // "0" .. "3" or "7": skip the timing, use this one
+  const char* force = std::getenv("SW_CGNE64");
+  if (force && ((force[0] >= '0' && force[0] <= '3') || force[0] == '7') && !force[1] &&
+      (force[0] != '7' || cgne64_staged_supported(L.nc)))
+    return force[0] - '0';
   const auto key = std::make_tuple(c->device, L.nc, 1, L.E0 * L.E1, sms);
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -338,7 +341,10 @@ static int cgne64_variant(sw_mg* mg, MgLevel& L, const double2* b, double2* x, i
   SW_CUDA(cudaEventCreate(&e0));
   SW_CUDA(cudaEventCreate(&e1));
   TuneRec best{0, 1e30};
-  for (int v = 0; v < 4; ++v) {
+  int cand[5] = {0, 1, 2, 3, 7};
+  const int ncand = cgne64_staged_supported(L.nc) ? 5 : 4;
+  for (int ci = 0; ci < ncand; ++ci) {
+    const int v = cand[ci];
     float tot = 0.f;
     for (int rep = 0; rep <= kReps; ++rep) {  // rep 0 is a warm-up
       SW_CUDA(cudaEventRecord(e0, c->stream));

@@ -268,10 +268,12 @@ bool launch_cgne_persistent(const CoarseGeom& g, const void* Y, int df64, const 
 // real FMAs per complex product, reading Ys = Re + Im of every entry of Y
 // (launch_sum_planes); variant 0: four FMAs on Y alone (Ys may be NULL);
 // variants 2 and 3: 0 and 1 with reduce-scatter row sums and a per-component
-// update.
+// update; variant 7: 3 with its operands staged in shared memory by
+// asynchronous copies (nc a multiple of 32, cgne64_staged_supported).
 // v4: 8 n doubles of 32-byte aligned scratch (forms of r and p).  False when
 // nc has no compiled variant.
 bool cgne64_supported(int nc);
+bool cgne64_staged_supported(int nc);
 void launch_sum_planes(const double2* Y, double* Ys, long n, cudaStream_t s);
 bool launch_cgne64(const CoarseGeom& g, int variant, const double2* Y, const double* Ys,
                    const double2* b, double2* x, double2* r, double2* p, double* v4,

@@ -309,8 +309,9 @@ def test_bench_workload_counts_match_oracle_record(sw, ctx):
 
 @pytest.mark.parametrize("nvec", [[8, 12], [24, 32]])
 def test_fp64_cgne_variants_agree(sw, ctx, monkeypatch, nvec):
-    """The four variants of the FP64 coarsest kernel (four- or three-FMA
-    products, full or reduce-scatter row sums) run the same iteration with
+    """The variants of the FP64 coarsest kernel (four- or three-FMA products,
+    full or reduce-scatter row sums, operands staged in shared memory) run the
+    same iteration with
     different rounding: each solve reaches 1e-10 by the oracle's D and the
     solutions agree to the solve tolerance; coarse dof 24 and 64.  The counts
     agree only loosely: a coarsest CGNE of 1024 dof stopped at 0.2 takes
@@ -325,7 +326,7 @@ def test_fp64_cgne_variants_agree(sw, ctx, monkeypatch, nvec):
     g = sw.sw_gauge_load(ctx, th)
     b = si.gaussian_complex(1004, L * L)
     out = {}
-    for v in ("0", "1", "2", "3"):
+    for v in ("0", "1", "2", "3", "7"):  # 7 (staged operands) needs nc = 32 or 64
         monkeypatch.setenv("SW_CGNE64", v)
         h = sw.sw_mg_setup(g, m, 3, blocks, nvec, psi0=psi0)
         x = np.zeros_like(b)
@@ -334,7 +335,7 @@ def test_fp64_cgne_variants_agree(sw, ctx, monkeypatch, nvec):
         assert st["converged"] and np.linalg.norm(b - D @ x) / np.linalg.norm(b) <= 1e-10, v
         out[v] = (st, x)
     s0, x0 = out["0"]
-    for v in ("1", "2", "3"):
+    for v in ("1", "2", "3", "7"):
         s, x = out[v]
         assert np.linalg.norm(x - x0) / np.linalg.norm(x0) < 1e-7, v
         a0 = s0["coarsest_iters"] / s0["coarsest_solves"]
