@@ -642,6 +642,8 @@ def run_native(args, rank, world, local):
     # roofline of the dominant kernel (FP64 complex MAC = 8 flop; FP64-ALU bound on GB300):
     # the persistent coarsest CGNE (category 5: 2 stencil applications per iteration)
     # or a coarse stencil (categories 1, 2), whichever took the most time
+    # the FP64 pipe's measured rate at the clock of the run: the roofline's peak
+    fp64_peak = sw.sw_fp64_peak(ctx)
     shapes = {l: sw.sw_mg_level_info(h, l + 1) for l in (1, 2)}
     cand = {c: ktimes[c][1] for c in (1, 2, 5)}
     best = max(cand, key=cand.get)
@@ -680,16 +682,17 @@ def run_native(args, rank, world, local):
             traffic = per_iter * iters / max(n_l, 1)
     executed = (6.0 / 8.0 if (variant or 0) & 1 else 1.0) * achieved
     roof = {"bound": "alu", "kernel": kname,
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": traffic,
             "achieved_note": "algorithmic flops of the stencil products (8 per complex "
                              "multiply-add, the operation's definition) per launch / average "
                              "launch time; the three-FMA form executes 6 of them",
-            "executed_TFLOPs": executed, "executed_frac": executed / FP64_PEAK_TFLOPS,
+            "executed_TFLOPs": executed, "executed_frac": executed / fp64_peak,
             "traffic_note": "ncu dram bytes per CGNE iteration (profiles/k_cgne64_fp64_256.md) x "
                             "iterations per launch; null if the kernel changed since",
-            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 FMA probe: 1.196 "
-                           "TFLOP/s at 1995 MHz)",
+            "peak_source": "measured in this run by sw_fp64_peak (FP64 FMA throughput, 16 warps "
+                           "x 4 chains per SM); MEASURED_PEAKS.json has no FP64 entry",
+            "peak_nominal": FP64_PEAK_TFLOPS, "frac_of_nominal": achieved / FP64_PEAK_TFLOPS,
             "algorithmic_flop_per_launch": flop,
             "hbm_GBps_equiv": byt / dur / 1e9, "launches": n_l, "avg_us": dur * 1e6}
     names = {0: "S", 1: "A_hat_level2", 2: "A_hat_level3", 5: "cgne_persistent"}

@@ -311,6 +311,14 @@ int sw_set_timing(sw_ctx* ctx, int enable);
 int sw_kernel_times(sw_ctx* ctx, int n, long long* launches, double* ms);
 long long sw_launch_count(void);
 
+/* Measured FP64 throughput of the context's device in TFLOP/s (*tflops): one
+ * CTA of 16 warps per SM runs four independent chains of dependent FMAs per
+ * thread, timed with CUDA events on the context stream after a warm-up
+ * launch (two FLOPs per FMA).  It is the denominator of the FP64 kernels'
+ * roofline, at the clock the device runs when it is called.  Allocates and
+ * frees an SM-count x 512 array of doubles; synchronises the stream. */
+int sw_fp64_peak(sw_ctx* ctx, double* tflops);
+
 /* Failure-detection check of the persistent coarsest-level CGNE: runs it
  * once with one CTA withholding its arrival at the first grid barrier, so
  * every other CTA's bounded wait runs out (about a second).  Expected result:

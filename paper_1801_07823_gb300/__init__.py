@@ -23,7 +23,7 @@ __all__ = [
     "sw_mg_export_P", "sw_mg_export_Y", "sw_mg_apply_level", "sw_mg_transfer",
     "sw_stream_seed", "sw_set_timing", "sw_kernel_times", "sw_launch_count",
     "sw_dslash_schur_noalloc", "sw_debug_cgne_stall", "sw_cg_eo_solve", "sw_debug_batch_stall",
-    "sw_autotune_entries", "sw_mg_level_maps", "sw_context_set_sm_share",
+    "sw_autotune_entries", "sw_mg_level_maps", "sw_context_set_sm_share", "sw_fp64_peak",
 ]
 
 SW_OP_D, SW_OP_DDAG, SW_OP_A, SW_OP_ADAG, SW_OP_S, SW_OP_DNAIK, SW_OP_ANAIK = 0, 1, 2, 3, 4, 5, 6
@@ -106,6 +106,7 @@ def lib():
             "sw_autotune_entries": (_I, [_I, _VP, _VP, _VP, _VP, _VP]),
             "sw_mg_level_maps": (_I, [_VP, _I, _VP, _VP]),
             "sw_context_set_sm_share": (_I, [_VP, _I, _I]),
+            "sw_fp64_peak": (_I, [_VP, ctypes.POINTER(_D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -372,6 +373,13 @@ def sw_kernel_times(ctx: _Handle, n: int = 7):
 
 def sw_launch_count() -> int:
     return int(lib().sw_launch_count())
+
+
+def sw_fp64_peak(ctx: _Handle) -> float:
+    """Measured FP64 FMA throughput of the context's device, TFLOP/s."""
+    v = _D(0.0)
+    _check(lib().sw_fp64_peak(ctx.ptr, ctypes.byref(v)), ctx.ptr)
+    return float(v.value)
 
 
 def sw_dslash_schur_noalloc(g: _Handle, mass: float, inp, out):
