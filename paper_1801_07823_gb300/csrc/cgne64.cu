@@ -356,65 +356,116 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// This warp's chunks: chunk k is half h of direction d of unit m, the unit
+// being u0 + m 16 G (units are dealt to sub-partitions first, as in phase).
+template <int NC>
+struct StMap {
+  static constexpr int kUnitsPerSite = NC / kRows;
+  static constexpr int kHalves = NC / (kQ * kCh);  // chunks per direction
+  static constexpr int kItems = 5 * kHalves;       // chunks per unit
+  int G, lane, rr, q, u0, nk;
+  unsigned char* mine;  // this warp's three stages
+  __device__ StMap(const Args& a, unsigned char* smem) {
+    static_assert(NC % (kQ * kCh) == 0, "a direction must split into whole chunks");
+    G = gridDim.x;
+    const int warp = threadIdx.x >> 5;
+    lane = threadIdx.x & 31;
+    rr = lane >> 3;
+    q = lane & 7;
+    const int nunits = a.E0 * a.E1 * kUnitsPerSite;
+    u0 = (warp & 3) * G + blockIdx.x + 4 * G * (warp >> 2);
+    const int nmine = u0 < nunits ? (nunits - 1 - u0) / (16 * G) + 1 : 0;
+    nk = nmine * kItems;
+    mine = smem + (size_t)warp * kStages * kStageBytes;
+  }
+  __device__ void decode(int k, int& X, int& i, int& d, int& h) const {
+    const int m = k / kItems, rem = k - m * kItems;
+    d = rem / kHalves;
+    h = rem - d * kHalves;
+    const int u = u0 + m * 16 * G;
+    X = u / kUnitsPerSite;
+    i = (u - X * kUnitsPerSite) * kRows + rr;
+  }
+  __device__ unsigned char* stage(int k) const { return mine + (k % kStages) * kStageBytes; }
+};
+
+// Stencil rows and sum plane of chunk k (A: DAG = false; A^dag: true).
+template <int NC, bool DAG>
+__device__ __forceinline__ void st_stencil(const Args& a, const StMap<NC>& mp, int k,
+                                           unsigned long long pol) {
+  if (k >= mp.nk) return;
+  int X, i, d, h;
+  mp.decode(k, X, i, d, h);
+  const int nb = nbr(X, d, a.E0, a.E1);
+  const long base = DAG ? ((long)(nb * 5 + opp(d)) * NC + i) * NC + mp.q
+                        : ((long)(X * 5 + d) * NC + mp.q) * NC + i;
+  const long step = DAG ? kQ : (long)kQ * NC;
+  unsigned char* st = mp.stage(k);
+  double2* Yb = reinterpret_cast<double2*>(st);
+  double* Sb = reinterpret_cast<double*>(st + kCh * 32 * 16);
+#pragma unroll
+  for (int tt = 0; tt < kCh; ++tt) {
+    const long off = base + (long)(h * kCh + tt) * step;
+    cp16h(Yb + tt * 32 + mp.lane, a.Y + off, pol);
+    cp8h(Sb + tt * 32 + mp.lane, a.Ys + off, pol);
+  }
+}
+// Vector forms of chunk k: the entries v[nb NC + (h kCh + tt) 8 + q] are 32
+// consecutive V4s; lane copies entry `lane` (two 16-byte halves).
+template <int NC>
+__device__ __forceinline__ void st_vector(const Args& a, const StMap<NC>& mp, const V4* v,
+                                          int k) {
+  if (k >= mp.nk) return;
+  int X, i, d, h;
+  mp.decode(k, X, i, d, h);
+  const int nb = nbr(X, d, a.E0, a.E1);
+  V4* Wb = reinterpret_cast<V4*>(mp.stage(k) + kCh * 32 * 24);
+  const V4* src = v + (long)nb * NC + h * kCh * kQ + mp.lane;
+  cp16(Wb + mp.lane, src);
+  cp16(reinterpret_cast<unsigned char*>(Wb + mp.lane) + 16,
+       reinterpret_cast<const unsigned char*>(src) + 16);
+}
+
+// Issued before the grid barrier that precedes a phase: the stencil part of
+// the phase's first two chunks (one copy group each), which depends on
+// nothing the barrier waits for, so its latency overlaps the barrier.
+template <int NC, int MODE>
+__device__ void prefetch_st(const Args& a, unsigned long long pol, unsigned char* smem) {
+  const StMap<NC> mp(a, smem);
+  st_stencil<NC, MODE != kP1>(a, mp, 0, pol);
+  cp_commit();
+  st_stencil<NC, MODE != kP1>(a, mp, 1, pol);
+  cp_commit();
+}
+
+// The phase itself, after prefetch_st<NC, MODE>: groups A, B (stencil of
+// chunks 0, 1) are in flight; C, D bring their vector forms; then one group
+// per chunk, two chunks ahead, so that waiting for all but the two newest
+// groups always completes chunk k.
 template <int NC, int MODE>
 __device__ double phase_st(const Args& a, double coef, unsigned long long pol,
                            unsigned char* smem) {
-  static_assert(NC % (kQ * kCh) == 0, "a direction must split into whole chunks");
-  constexpr int kUnitsPerSite = NC / kRows;
-  constexpr int kHalves = NC / (kQ * kCh);  // chunks per direction
-  constexpr int kItems = 5 * kHalves;       // chunks per unit
+  constexpr int kUnitsPerSite = StMap<NC>::kUnitsPerSite;
+  constexpr int kItems = StMap<NC>::kItems;
   constexpr bool DAG = MODE != kP1;
-  const int G = gridDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = warp & 3, wj = warp >> 2;
-  const int rr = lane >> 3, q = lane & 7;
+  const StMap<NC> mp(a, smem);
+  const int G = mp.G, lane = mp.lane, rr = mp.rr, q = mp.q, u0 = mp.u0, nk = mp.nk;
   const int comp = (q >> 2) & 1;
   const bool writer = (q & 3) == 0;
-  const int nunits = a.E0 * a.E1 * kUnitsPerSite;
-  const int u0 = sub * G + blockIdx.x + 4 * G * wj;  // this warp's units: u0 + m 16 G
-  const int nmine = u0 < nunits ? (nunits - 1 - u0) / (16 * G) + 1 : 0;
-  const int nk = nmine * kItems;
   const V4* v = MODE == kP1 ? a.p4 : a.r4;
-  unsigned char* mine = smem + (size_t)warp * kStages * kStageBytes;
-  // chunk k into stage k % 3 (an empty group past the end keeps the counting uniform)
-  auto issue = [&](int k) {
-    if (k < nk) {
-      const int m = k / kItems, rem = k - m * kItems, d = rem / kHalves, h = rem - d * kHalves;
-      const int u = u0 + m * 16 * G;
-      const int X = u / kUnitsPerSite;
-      const int i = (u - X * kUnitsPerSite) * kRows + rr;
-      const int nb = nbr(X, d, a.E0, a.E1);
-      const long base = DAG ? ((long)(nb * 5 + opp(d)) * NC + i) * NC + q
-                            : ((long)(X * 5 + d) * NC + q) * NC + i;
-      const long step = DAG ? kQ : (long)kQ * NC;
-      unsigned char* st = mine + (k % kStages) * kStageBytes;
-      double2* Yb = reinterpret_cast<double2*>(st);
-      double* Sb = reinterpret_cast<double*>(st + kCh * 32 * 16);
-      V4* Wb = reinterpret_cast<V4*>(st + kCh * 32 * 24);
-#pragma unroll
-      for (int tt = 0; tt < kCh; ++tt) {
-        const long off = base + (long)(h * kCh + tt) * step;
-        cp16h(Yb + tt * 32 + lane, a.Y + off, pol);
-        cp8h(Sb + tt * 32 + lane, a.Ys + off, pol);
-      }
-      // the chunk's vector forms v[nb NC + (h kCh + tt) 8 + q] are 32
-      // consecutive entries: lane copies entry `lane` (two 16-byte halves)
-      const V4* src = v + (long)nb * NC + h * kCh * kQ + lane;
-      cp16(Wb + lane, src);
-      cp16(reinterpret_cast<unsigned char*>(Wb + lane) + 16,
-           reinterpret_cast<const unsigned char*>(src) + 16);
-    }
-    cp_commit();
-  };
   double acc = 0.0, K1 = 0.0, K2 = 0.0, K3 = 0.0;
-  issue(0);
-  issue(1);
+  st_vector<NC>(a, mp, v, 0);
+  cp_commit();
+  st_vector<NC>(a, mp, v, 1);
+  cp_commit();
   for (int k = 0; k < nk; ++k) {  // warp-uniform
     __syncwarp();  // every lane is done with chunk k - 1, whose stage chunk k + 2 reuses
-    issue(k + 2);
+    st_stencil<NC, DAG>(a, mp, k + 2, pol);
+    st_vector<NC>(a, mp, v, k + 2);
+    cp_commit();  // (an empty group past the end keeps the counting uniform)
     cp_wait<2>();  // this lane's copies of chunk k have landed
     __syncwarp();  // and so have the other lanes' (vector forms are shared)
-    const unsigned char* st = mine + (k % kStages) * kStageBytes;
+    const unsigned char* st = mp.stage(k);
     const double2* Yb = reinterpret_cast<const double2*>(st);
     const double* Sb = reinterpret_cast<const double*>(st + kCh * 32 * 16);
     const V4* Wb = reinterpret_cast<const V4*>(st + kCh * 32 * 24);
@@ -535,6 +586,17 @@ __device__ __forceinline__ double run_phase(const Args& a, double coef, unsigned
     return phase<NC, M3, MODE>(a, coef, pol);
 }
 
+// The staged variant's pre-barrier copies of the next phase (no-op otherwise).
+template <int NC, bool ST, int MODE>
+__device__ __forceinline__ void prefetch(const Args& a, unsigned long long pol,
+                                         unsigned char* smem) {
+  if constexpr (ST) prefetch_st<NC, MODE>(a, pol, smem);
+}
+// Every exit first waits for this thread's asynchronous copies still in flight
+// (the staged variant prefetches ahead of barriers), so that none lands in
+// shared memory after the CTA has left.
+__device__ __forceinline__ void leave() { cp_wait<0>(); }
+
 template <int NC, bool M3, bool RS, bool ST>
 __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
   extern __shared__ __align__(128) unsigned char stage_smem[];  // staged variant only
@@ -558,9 +620,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     acc = fma(v.x, v.x, fma(v.y, v.y, acc));
   }
   int ph = 0;
+  prefetch<NC, ST, kInit>(a, pol, stage_smem);
   cta_partial(acc, red, a.partials + ph * gridDim.x);
-  if (a.stall_test && blockIdx.x == 0) return;  // the others' first wait must run out
-  if (!grid_barrier(a.bar, a.status, ++gen)) return;
+  if (a.stall_test && blockIdx.x == 0) return leave();  // the others' first wait must run out
+  if (!grid_barrier(a.bar, a.status, ++gen)) return leave();
   {
     const double rr0 = grid_sum(a.partials + ph * gridDim.x, &bcast);
     if (threadIdx.x == 0) {
@@ -576,12 +639,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
       a.status[0] = 0;
       if (sh_state == 2) a.status[2] = 1;
     }
-    return;
+    return leave();
   }
   // p = A^dag r, ||p||^2
   acc = run_phase<NC, M3, RS, ST, kInit>(a, 0.0, pol, stage_smem);
+  prefetch<NC, ST, kP1>(a, pol, stage_smem);
   cta_partial(acc, red, a.partials + ph * gridDim.x);
-  if (!grid_barrier(a.bar, a.status, ++gen)) return;
+  if (!grid_barrier(a.bar, a.status, ++gen)) return leave();
   {
     const double pp = grid_sum(a.partials + ph * gridDim.x, &bcast);
     if (threadIdx.x == 0) sh_coef = sh_rr / pp;  // alpha
@@ -591,8 +655,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
   int k = 0;
   for (;;) {
     acc = run_phase<NC, M3, RS, ST, kP1>(a, sh_coef, pol, stage_smem);  // w = A p; x += alpha p; r -= alpha w
+    prefetch<NC, ST, kP2>(a, pol, stage_smem);  // unused if this was the last iteration
     cta_partial(acc, red, a.partials + ph * gridDim.x);
-    if (!grid_barrier(a.bar, a.status, ++gen)) return;
+    if (!grid_barrier(a.bar, a.status, ++gen)) return leave();
     ++k;
     {
       const double rr_new = grid_sum(a.partials + ph * gridDim.x, &bcast);
@@ -609,8 +674,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     ph ^= 1;
     if (sh_state) break;
     acc = run_phase<NC, M3, RS, ST, kP2>(a, sh_coef, pol, stage_smem);  // p = A^dag r + beta p
+    prefetch<NC, ST, kP1>(a, pol, stage_smem);
     cta_partial(acc, red, a.partials + ph * gridDim.x);
-    if (!grid_barrier(a.bar, a.status, ++gen)) return;
+    if (!grid_barrier(a.bar, a.status, ++gen)) return leave();
     {
       const double pp = grid_sum(a.partials + ph * gridDim.x, &bcast);
       if (threadIdx.x == 0) sh_coef = sh_rr / pp;  // alpha
@@ -622,6 +688,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgne64(Args a) {
     a.status[0] = k;
     if (sh_state == 2) a.status[2] = 1;
   }
+  leave();
 }
 
 __global__ void k_sum_planes(const double2* __restrict__ Y, double* __restrict__ Ys, long n) {
