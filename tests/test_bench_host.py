@@ -58,3 +58,26 @@ def test_reference_arm_bounded_sample(tmp_path, monkeypatch, capsys):
 
     bench.run_reference(Other, 0, 1)
     assert "unavailable" in json.loads(capsys.readouterr().out)
+
+
+def test_profiled_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu summary only while
+    the kernel source still has the SHA-1 the summary records: the current
+    profile matches the current source, and a changed source (or a missing
+    key) gives None instead of a stale figure."""
+    import hashlib
+    import os
+    v = bench._profiled_traffic("k_cgne64_fp64_256.md", "paper_1801_07823_gb300/csrc/cgne64.cu",
+                                "dram_bytes_per_iteration")
+    assert v is not None and v > 0
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "src.cu").write_text("kernel v1\n")
+    sha = hashlib.sha1(b"kernel v1\n").hexdigest()
+    (tmp_path / "profiles" / "p.md").write_text(
+        f"dram_bytes_per_iteration: 1234\nsource_sha1 (src.cu): {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._profiled_traffic("p.md", "src.cu", "dram_bytes_per_iteration") == 1234.0
+    assert bench._profiled_traffic("p.md", "src.cu", "other_key") is None
+    (tmp_path / "src.cu").write_text("kernel v2\n")
+    assert bench._profiled_traffic("p.md", "src.cu", "dram_bytes_per_iteration") is None
+    assert os.path.exists(tmp_path / "profiles" / "p.md")
